@@ -1,0 +1,350 @@
+"""Throughput of the GB300 LGF-FMM solve, one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one whole solve u = G * f (every step of Sec. 3.1: forward FFTs,
+regularization, near-field and interaction-list products, inverse FFTs,
+interpolation) on the 128^3 torus workload (8^3 blocks of 16^3 points, 3
+levels, interpolation order 8) in FP32, inputs resident in HBM.  L2 is flushed
+(a 256 MiB write) before every timed step; steps are timed with CUDA events on
+the solve stream.  Under torchrun each rank solves its own replica (weak
+scaling, no data-path collective); rank 0 prints the max-over-ranks timing.
+
+--impl reference times the CPU oracle (NumPy FP64, the paper's method step by
+step) on the host cores, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "LGF-FMM points/s at <=1e-5 rel err, FP32 vs FP64 on 1 GB300; serve p50/p99 ms"
+WORKLOAD = "torus_box_128"
+FP32_FMA_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def interaction_pairs(blocks: np.ndarray, n_levels: int):
+    """Source-target interval pairs per level: level 0 near pairs, level l >= 1
+    interaction-list pairs (Sec. 3.1 lists), for the roofline's work count."""
+    out = {}
+    b = np.asarray(blocks, dtype=np.int64)
+    for l in range(0, n_levels):
+        iv = np.unique(b >> max(l - 1, 0), axis=0)
+        keys = set(map(tuple, iv))
+        n = 0
+        for p in map(tuple, iv):
+            if l == 0:
+                n += sum((p[0] + dx, p[1] + dy, p[2] + dz) in keys
+                         for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1))
+                continue
+            pp = (p[0] >> 1, p[1] >> 1, p[2] >> 1)
+            for ex in (-1, 0, 1):
+                for ey in (-1, 0, 1):
+                    for ez in (-1, 0, 1):
+                        for c in range(8):
+                            q = (2 * (pp[0] + ex) + (c & 1), 2 * (pp[1] + ey) + ((c >> 1) & 1),
+                                 2 * (pp[2] + ez) + (c >> 2))
+                            if q in keys and max(abs(q[0] - p[0]), abs(q[1] - p[1]), abs(q[2] - p[2])) > 1:
+                                n += 1
+        out[l] = n
+    return out
+
+
+def cpu_oracle_rate(p, spectra=None):
+    """Oracle FMM on the host cores: (points/s, seconds, cores used, solution)."""
+    from oracle import fmm
+    sp = spectra if spectra is not None else fmm.Spectra(p.n_b)
+    if spectra is None:      # kernel spectra are plan-time work: precompute outside the timing
+        fmm.fmm_solve(p.blocks[:1], p.f[:1], p.n_b, 1, p.order, spectra=sp)
+    t0, c0 = time.perf_counter(), time.process_time()
+    u = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order, spectra=sp)
+    dt, dc = time.perf_counter() - t0, time.process_time() - c0
+    return p.n_points / dt, dt, max(1, round(dc / dt)), u
+
+
+def reference_sample():
+    """Bounded sample of the workload for the CPU arm: the 64^3 window (4^3
+    blocks of 16^3, 2 levels) of the 128^3 torus at the same order."""
+    full = W.config(1)
+    sel = np.all(full.blocks < 4, axis=1)
+    return W.Problem(full.blocks[sel].copy(), full.f[sel].copy(), 16, 2, full.order, "torus_box_128_window64")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import fmm
+    p = reference_sample()
+    sp = fmm.Spectra(p.n_b)
+    for _ in range(args.warmup):
+        fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order, spectra=sp)
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(args.steps):
+        fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order, spectra=sp)
+    dt, dc = time.perf_counter() - t0, time.process_time() - c0
+    value = p.n_points * args.steps / dt
+    cores = max(1, round(dc / dt))
+    sample = "oracle FMM (NumPy FP64) on the 64^3 window (4^3 blocks of 16^3, 2 levels, order 8) of the 128^3 torus"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "window64", "points": p.n_points},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import paper_1402_6081_gb300 as lgfm
+    from paper_1402_6081_gb300 import build as lgf_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        lgf_build.build()
+    if dist is not None:
+        dist.barrier()
+    lgfm.library()
+    dev = torch.cuda.current_device()
+
+    p = W.config(1)
+    npts = p.n_points
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec)
+        f = torch.from_numpy(p.f).to(dt).cuda()
+        u = torch.empty_like(f)
+        return s, f, u
+
+    def timed_steps(s, f, u, steps, warmup, timing_capacity=0):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                s(f, u, stream)
+        torch.cuda.synchronize()
+        if timing_capacity:
+            lgfm.lgf_plan_set_timing(s.plan, timing_capacity)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                flush.fill_(1.0)
+                a.record(stream)
+                s(f, u, stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist is not None:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, wall
+
+    s32, f32, u32 = make(lgfm.LGF_FP32)
+    with torch.cuda.stream(stream):
+        s32(f32, u32, stream)
+    torch.cuda.synchronize()
+    per_solve_launches = None
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms, wall = timed_steps(s32, f32, u32, args.steps, args.warmup, timing_capacity=args.steps * 16)
+    clk = clocks.stop()
+    ktimes, per_solve_launches = lgfm.lgf_plan_timings(s32.plan)
+    lgfm.lgf_plan_set_timing(s32.plan, 0)
+    total_ms = float(sum(ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * npts * args.steps / (total_ms * 1e-3)
+
+    # FP64 form on the same GPU (shorter run)
+    s64, f64, u64 = make(lgfm.LGF_FP64)
+    k64 = max(3, min(50, args.steps // 20))
+    ms64, _ = timed_steps(s64, f64, u64, k64, 3)
+    rate64 = npts / (statistics.mean(ms64) * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    fh = torch.from_numpy(p.f).float().pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    k_e2e = max(3, min(500, args.steps // 4))
+    for _ in range(3):
+        lgfm.lgf_solve_host(s32.plan, fh, uh, stream)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        lgfm.lgf_solve_host(s32.plan, fh, uh, stream)
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+
+    # roofline of the dominant kernel
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_tot, dom_cnt) = dom
+    dom_ms = dom_tot / dom_cnt
+    pk, src = peaks()
+    pairs = interaction_pairs(p.blocks, p.n_levels)
+    S0, SI = 2 * p.n_b, 36
+    nw = {0: (S0 // 2 + 1) * S0 * S0, 1: (SI // 2 + 1) * SI * SI}
+    roof = None
+    if dom_name.startswith("mac_"):
+        lvl = 0 if dom_name == "mac_level0" else 1
+        flops = 8.0 * pairs[lvl] * nw[lvl]                 # one complex MAC = 8 real flops
+        peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
+        ach = flops / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
+                "algorithmic": f"8 flop x {pairs[lvl]} interaction pairs x {nw[lvl]} frequencies"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": None, "peak": pk.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": npts, "blocks": len(p.blocks), "n_b": p.n_b,
+                   "levels": p.n_levels, "interp_order": p.order, "fft_sizes": [S0, SI],
+                   "l2": "flushed: 256 MiB write before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": rate64, "unit": "points/s", "ms_per_step": statistics.mean(ms64), "steps": k64},
+        "e2e": {"value": npts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(fh.numel() * 4),
+                "d2h_bytes_per_step": int(uh.numel() * 4), "steps": k_e2e},
+        "gpu_launches": int(per_solve_launches) * args.steps,
+        "launches_per_step": int(per_solve_launches),
+        "kernel_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
+        "roofline": roof, "peaks": src,
+        "clocks": clk, "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import fmm
+        rate, secs, cores, uref = cpu_oracle_rate(p)
+        torch.cuda.synchronize()
+        got = u32.double().cpu().numpy()
+        out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                               "sample": f"one full oracle FMM solve of the 128^3 torus ({secs:.1f} s, "
+                                         "kernel spectra precomputed outside the timing)"}
+        out["rel_err_fp32_vs_oracle"] = fmm.rel_linf(got, uref)
+        out["rel_err_fp64_vs_oracle"] = fmm.rel_linf(u64.double().cpu().numpy(), uref)
+    if rank == 0:
+        print(json.dumps(out))
+    s32.close()
+    s64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

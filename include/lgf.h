@@ -1,0 +1,160 @@
+/*
+ * lgf.h - C ABI of the GB300 LGF fast multipole solver.
+ *
+ * Solves the discrete Poisson problem  L u = f  on an unbounded 3D lattice
+ * (Eq. dpoisson: L is the 7-point Laplacian with unit spacing), where f is
+ * supported on a set of equal cubic blocks of n_b^3 points (Sec. 2.3), and u
+ * is wanted on the same blocks.  The solution is the lattice convolution
+ * u = G * f with the lattice Green's function G (Eq. dpoissonsoln), evaluated
+ * by the Fast Lattice Green's Function method of Sec. 3.1: block and interval
+ * convolutions done as zero-padded FFT convolutions against precomputed
+ * kernel spectra (Sec. 2.2, Eq. precomp), a multilevel octree of interpolation
+ * intervals with n_I = n_b + 1 equispaced nodes per axis (Sec. 4), Lagrange
+ * interpolation with at most n_max = interp_order + 1 nodes per point (Sec. 2.5)
+ * and its adjoint for regularization (Sec. 2.4).
+ *
+ * Data layout (caller side).  A field is n_blocks * n_b^3 values of the plan's
+ * precision (float for LGF_FP32, double for LGF_FP64).  Block b (in the order
+ * of block_ijk given at plan creation) owns values [b*n_b^3, (b+1)*n_b^3); its
+ * point (i, j, k) is value i + n_b*(j + n_b*k) and sits at lattice point
+ * block_ijk[b]*n_b + (i, j, k).
+ *
+ * Errors.  Every call returns an lgf_status; nothing else crosses the ABI.
+ * lgf_last_error() returns a message for the calling thread's last failure.
+ * Launch errors surface at the call; faults inside an asynchronous solve
+ * surface at lgf_plan_sync() or at the next CUDA call on that stream.
+ *
+ * Concurrency.  A plan owns its device workspace, so one plan must not run two
+ * solves at once (two streams, or two host threads).  Different plans are
+ * independent.  Kernel spectra are shared between plans with equal (n_b,
+ * precision) through a reference-counted cache; its entries live until the
+ * last plan using them is destroyed.
+ *
+ * Device.  A plan is bound to the CUDA device current at lgf_plan_create; all
+ * later calls on it must run with that device current.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_plan_s *lgf_plan;
+
+typedef enum {
+    LGF_OK = 0,
+    LGF_ERR_INVALID_ARG = 1,   /* bad pointer, size, duplicate block, ...     */
+    LGF_ERR_UNSUPPORTED = 2,   /* valid request this build does not handle     */
+    LGF_ERR_OOM = 3,           /* device or host allocation failed            */
+    LGF_ERR_CUDA = 4,          /* CUDA runtime error (message has details)     */
+    LGF_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
+    LGF_ERR_BUDGET = 6         /* request exceeds a caller-given memory budget */
+} lgf_status;
+
+typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
+
+/* Arithmetic of the regularization / interpolation contractions (Eqs. alg_reg,
+ * alg_interp).  NATIVE uses the plan precision on the CUDA cores. */
+typedef enum { LGF_INTERP_NATIVE = 0 } lgf_interp_mode;
+
+/*
+ * lgf_plan_create - build the tree, lists, interpolation stencils and kernel
+ * spectra for one block set (Sec. 3.1 Step 0 and Sec. 3.1 lists), and
+ * allocate the device workspace of a solve.
+ *
+ *   block_ijk     host array, n_blocks x 3 int32 block indices (x, y, z);
+ *                 unique; copied, the caller keeps ownership
+ *   n_blocks      >= 1
+ *   n_b           points per block edge: 4, 8 or 16
+ *   n_levels      L >= 1: the leaves are level 1 and the root level is L
+ *                 (Sec. 3.1).  Level L must hold intervals that are all near
+ *                 one another (at most two per axis, aligned); otherwise
+ *                 LGF_ERR_UNSUPPORTED with a message naming the needed depth.
+ *   interp_order  polynomial degree p of the interpolation; n_max = p + 1
+ *                 nodes are used per point, 1 <= n_max <= n_b + 1
+ *   precision     LGF_FP32 or LGF_FP64 (FFTs, products and interpolation);
+ *                 the LGF values and spectra are always generated in FP64
+ *   interp_mode   LGF_INTERP_NATIVE
+ *   out           receives the plan
+ *
+ * Runs on the host plus uploads on the current device; synchronous.
+ */
+lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n_b,
+                           int32_t n_levels, int32_t interp_order, int32_t precision,
+                           int32_t interp_mode, lgf_plan *out);
+
+/* Device bytes the plan holds (workspace plus its share of cached spectra);
+ * what a serving loop charges against its HBM budget. */
+lgf_status lgf_plan_workspace_bytes(lgf_plan plan, size_t *bytes);
+
+/* Points (n_blocks * n_b^3) of the plan. */
+lgf_status lgf_plan_points(lgf_plan plan, int64_t *n_points);
+
+/*
+ * lgf_solve - u = G * f on the plan's blocks (Sec. 3.1 Steps 1-3).
+ *   f_dev   device pointer, n_points values of the plan precision (read only)
+ *   u_dev   device pointer, n_points values (written in full, never read);
+ *           must not overlap f_dev
+ *   stream  a cudaStream_t (NULL = legacy default stream)
+ * Asynchronous on stream; every kernel of the solve runs on it.
+ */
+lgf_status lgf_solve(lgf_plan plan, const void *f_dev, void *u_dev, void *stream);
+
+/*
+ * lgf_solve_batch - n independent solves issued back to back on one stream.
+ * plans[i] / f_dev[i] / u_dev[i] as for lgf_solve; the plans must be distinct.
+ */
+lgf_status lgf_solve_batch(const lgf_plan *plans, const void *const *f_dev,
+                           void *const *u_dev, int32_t n, void *stream);
+
+/*
+ * lgf_solve_host - lgf_solve with host buffers: copies f to the plan's device
+ * staging buffer, solves, copies u back, and waits for the stream.
+ *   f_host, u_host  host pointers of n_points values (pinned memory is faster)
+ */
+lgf_status lgf_solve_host(lgf_plan plan, const void *f_host, void *u_host, void *stream);
+
+/* Waits for the plan's last solve and reports any asynchronous error. */
+lgf_status lgf_plan_sync(lgf_plan plan);
+
+/*
+ * Per-kernel timing (tracing).  lgf_plan_set_timing(plan, capacity) makes the
+ * next solves bracket each kernel launch by a CUDA event pair on the solve's
+ * stream, for up to `capacity` launches in total (0 turns it off).
+ * lgf_plan_timings waits for those events and returns, per kernel name, the
+ * summed elapsed time and the number of launches, then starts a new tally.
+ *   names               max_kernels x 32 chars (NUL-terminated names)
+ *   total_ms, count     max_kernels entries
+ *   n_kernels           receives the number of distinct names (may exceed max)
+ *   launches_per_solve  receives the kernel launches of the last solve (or NULL)
+ */
+lgf_status lgf_plan_set_timing(lgf_plan plan, int32_t capacity);
+lgf_status lgf_plan_timings(lgf_plan plan, int32_t max_kernels, int32_t *n_kernels, char *names,
+                            double *total_ms, int32_t *count, int32_t *launches_per_solve);
+
+/* Frees the plan and its workspace (waits for its device work first). */
+lgf_status lgf_destroy(lgf_plan plan);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *lgf_last_error(void);
+
+/*
+ * Host-side pieces of the plan builder, exposed for checking.
+ *
+ * lgf_green_values - G(n) of the 7-point Laplacian (App. A, Eq. lgf3) in FP64
+ *   for n triples (n x 3 int32, any signs) into out (n doubles); host only.
+ * lgf_interp_weights - the 1D interpolation matrices W[c][i][p], c = 0, 1 (2 x
+ *   (n_b+1) x (n_b+1) doubles): weight of parent node p for node i of child c
+ *   (Sec. 2.5 with the nearest-n_max rule); Reg applies the transpose.
+ */
+lgf_status lgf_green_values(const int32_t *n, int64_t count, double *out);
+lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double *W);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

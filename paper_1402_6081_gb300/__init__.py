@@ -1,0 +1,223 @@
+"""GB300-native LGF fast multipole solver (Liska & Colonius, "A parallel fast
+multipole method for elliptic difference equations").
+
+Thin Python binding of the C ABI in include/lgf.h: the functions below carry the
+same names and only marshal arguments (NumPy arrays, torch CUDA tensors, CUDA
+streams) into the library; every step of a solve runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing, importing a
+function raises.  Build it with ``paper_1402_6081_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+LGF_OK = 0
+LGF_FP64 = 0
+LGF_FP32 = 1
+LGF_INTERP_NATIVE = 0
+
+_STATUS = {0: "LGF_OK", 1: "LGF_ERR_INVALID_ARG", 2: "LGF_ERR_UNSUPPORTED", 3: "LGF_ERR_OOM",
+           4: "LGF_ERR_CUDA", 5: "LGF_ERR_TIMEOUT", 6: "LGF_ERR_BUDGET"}
+
+LIB_PATH = pathlib.Path(__file__).resolve().parent / "_build" / "liblgf.so"
+
+# every entry point of include/lgf.h with its ctypes signature
+_SIGS = {
+    "lgf_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "lgf_plan_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "lgf_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p]),
+    "lgf_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "lgf_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "lgf_last_error": (ctypes.c_char_p, []),
+    "lgf_green_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "lgf_interp_weights": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_1402_6081_gb300.build.build())")
+        h = ctypes.CDLL(str(LIB_PATH))
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != LGF_OK:
+        raise LgfError(status, where, library().lgf_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def _dev_ptr(t) -> int:
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous CUDA tensor")
+        return t.data_ptr()
+    return int(t)
+
+
+def lgf_last_error() -> str:
+    return library().lgf_last_error().decode()
+
+
+def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
+                    precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE) -> int:
+    """Plan for the block list ``blocks`` ((n, 3) block indices); returns the handle."""
+    b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
+    out = ctypes.c_void_p()
+    _check(library().lgf_plan_create(b.ctypes.data, len(b), n_b, n_levels, interp_order,
+                                     precision, interp_mode, ctypes.byref(out)), "lgf_plan_create")
+    return out.value
+
+
+def lgf_plan_workspace_bytes(plan: int) -> int:
+    v = ctypes.c_size_t()
+    _check(library().lgf_plan_workspace_bytes(plan, ctypes.byref(v)), "lgf_plan_workspace_bytes")
+    return v.value
+
+
+def lgf_plan_points(plan: int) -> int:
+    v = ctypes.c_int64()
+    _check(library().lgf_plan_points(plan, ctypes.byref(v)), "lgf_plan_points")
+    return v.value
+
+
+def lgf_solve(plan: int, f, u, stream=None) -> None:
+    """u = G * f on the plan's blocks; f, u contiguous CUDA tensors (or device
+    addresses) of the plan precision; asynchronous on ``stream``."""
+    _check(library().lgf_solve(plan, _dev_ptr(f), _dev_ptr(u), _stream_ptr(stream)), "lgf_solve")
+
+
+def lgf_solve_batch(plans, fs, us, stream=None) -> None:
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*plans)
+    F = (ctypes.c_void_p * n)(*[_dev_ptr(f) for f in fs])
+    U = (ctypes.c_void_p * n)(*[_dev_ptr(u) for u in us])
+    _check(library().lgf_solve_batch(P, F, U, n, _stream_ptr(stream)), "lgf_solve_batch")
+
+
+def lgf_solve_host(plan: int, f_host, u_host, stream=None) -> None:
+    """Solve with host buffers (NumPy arrays or CPU tensors, pinned preferred)."""
+    fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data
+    up = u_host.data_ptr() if hasattr(u_host, "data_ptr") else u_host.ctypes.data
+    _check(library().lgf_solve_host(plan, fp, up, _stream_ptr(stream)), "lgf_solve_host")
+
+
+def lgf_plan_sync(plan: int) -> None:
+    _check(library().lgf_plan_sync(plan), "lgf_plan_sync")
+
+
+def lgf_plan_set_timing(plan: int, capacity: int) -> None:
+    _check(library().lgf_plan_set_timing(plan, capacity), "lgf_plan_set_timing")
+
+
+def lgf_plan_timings(plan: int):
+    """{kernel name: (total_ms, launches)} since the last call, and the kernel
+    launches of the last solve."""
+    mx = 64
+    n = ctypes.c_int32()
+    names = ctypes.create_string_buffer(32 * mx)
+    tot = (ctypes.c_double * mx)()
+    cnt = (ctypes.c_int32 * mx)()
+    per = ctypes.c_int32()
+    _check(library().lgf_plan_timings(plan, mx, ctypes.byref(n), names, tot, cnt, ctypes.byref(per)),
+           "lgf_plan_timings")
+    out = {}
+    for j in range(min(n.value, mx)):
+        nm = names.raw[32 * j: 32 * (j + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (tot[j], cnt[j])
+    return out, per.value
+
+
+def lgf_destroy(plan: int) -> None:
+    _check(library().lgf_destroy(plan), "lgf_destroy")
+
+
+def lgf_green_values(n) -> np.ndarray:
+    """The library's FP64 G(n) for integer triples n (..., 3)."""
+    a = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(-1, 3))
+    out = np.empty(len(a))
+    _check(library().lgf_green_values(a.ctypes.data, len(a), out.ctypes.data), "lgf_green_values")
+    return out.reshape(np.shape(n)[:-1])
+
+
+def lgf_interp_weights(n_b: int, n_max: int) -> np.ndarray:
+    W = np.empty((2, n_b + 1, n_b + 1))
+    _check(library().lgf_interp_weights(n_b, n_max, W.ctypes.data), "lgf_interp_weights")
+    return W
+
+
+class Solver:
+    """Owns one plan: ``Solver(blocks, n_b, n_levels, order, precision)(f) -> u``
+    with f, u torch CUDA tensors of shape (n_blocks, n_b, n_b, n_b)."""
+
+    def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32):
+        self.n_b = n_b
+        self.precision = precision
+        self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
+        self.plan = lgf_plan_create(blocks, n_b, n_levels, interp_order, precision)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == LGF_FP64 else torch.float32
+
+    def __call__(self, f, u=None, stream=None):
+        import torch
+        if u is None:
+            u = torch.empty_like(f)
+        if f.dtype != self.dtype or u.dtype != self.dtype:
+            raise TypeError(f"expected {self.dtype} tensors")
+        if f.numel() != self.n_blocks * self.n_b ** 3 or u.numel() != f.numel():
+            raise ValueError("f/u size does not match the plan")
+        lgf_solve(self.plan, f, u, stream)
+        return u
+
+    def workspace_bytes(self) -> int:
+        return lgf_plan_workspace_bytes(self.plan)
+
+    def close(self):
+        if self.plan:
+            lgf_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,26 @@
+// Instantiation of the solve kernels for T = float.
+#include <cmath>
+
+#include "kernels_impl.cuh"
+
+namespace lgf {
+
+template <>
+cudaError_t Launch<float>::init_twiddles() {
+    float c[dev::kTwTotal], s[dev::kTwTotal];
+    for (int S : dev::kTwSizes) {
+        const int o = dev::tw_offset(S);
+        for (int j = 0; j < S; ++j) {
+            const double a = 2.0 * M_PI * double(j) / double(S);
+            c[o + j] = float(std::cos(a));
+            s[o + j] = float(std::sin(a));
+        }
+    }
+    cudaError_t e = cudaMemcpyToSymbol(dev::c_cos_f, c, sizeof(c));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(dev::c_sin_f, s, sizeof(s));
+    return e;
+}
+
+template struct Launch<float>;
+
+}  // namespace lgf

@@ -1,0 +1,76 @@
+// Internal declarations shared by the host plan builder and the CUDA kernels.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime_api.h>
+
+#include "../../include/lgf.h"
+
+namespace lgf {
+
+// ---- status helpers (thread-local message, see lgf_last_error) ----
+lgf_status fail(lgf_status code, const std::string& msg);
+lgf_status ok();
+
+// ---- FP64 LGF (green.cpp) ----
+void green_sorted(const std::vector<std::array<int, 3>>& trip, std::vector<double>& out);
+std::shared_ptr<const std::vector<double>> green_abs_table(int h, int V);
+
+// ---- host FP64 FFT (host_fft.cpp) ----
+// In-place complex DFT of length n with sign -1 (forward) or +1 (inverse,
+// unnormalised), on a strided sequence.
+void fft_inplace(std::complex<double>* x, int n, int stride, int sign);
+// count lines at base + c*line_stride, each n elements at stride (n <= 64).
+void fft_lines(std::complex<double>* base, int n, int stride, int count, int64_t line_stride,
+               int sign);
+
+// ---- interpolation stencils (plan.cpp) ----
+// W[c][i][p] (2 x n_I x n_I) for child c node i and parent node p.
+std::vector<double> interp_weights(int n_b, int n_max);
+
+// ---- FFT sizes ----
+// Level 0 pads a block of n_b to S0 = 2 n_b per axis; levels >= 1 pad an
+// interval of n_I = n_b + 1 nodes to S_I (>= 2 n_I - 1).  R2C keeps
+// NX = S/2 + 1 frequencies along x; a spectrum has NW = NX * S * S entries,
+// indexed w = (kz * S + ky) * NX + kx.
+inline int s_level0(int n_b) { return 2 * n_b; }
+int s_interval(int n_b);
+inline int nx_of(int S) { return S / 2 + 1; }
+inline int64_t nw_of(int S) { return int64_t(nx_of(S)) * S * S; }
+
+// ---- kernel-side parameter blocks ----
+struct R2CItem { int src; int dst; };      // source index -> spectrum slot
+struct C2RItem { int src; int dst; int aux; };
+
+// Launchers (kernels.cu); T = float or double.  All asynchronous on `stream`.
+template <typename T>
+struct Launch {
+    // Twiddle tables into constant memory of the current device.
+    static cudaError_t init_twiddles();
+    // R2C of items: input n_in^3 (stride n_in) zero-padded to S^3.
+    static cudaError_t r2c(int S, int n_in, const T* src, int64_t src_stride,
+                           const R2CItem* items, int n_items, void* spec, cudaStream_t st);
+    // C2R of items, truncated to n_out^3, written to dst[item.dst*n_out^3] (+add).
+    static cudaError_t c2r(int S, int n_out, const void* spec, const C2RItem* items, int n_items,
+                           T* dst, int64_t dst_stride, const T* add, int add_n, int64_t add_stride,
+                           cudaStream_t st);
+    static cudaError_t mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr,
+                                  int n_groups, int S, cudaStream_t st);
+    static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
+                                    int n_groups, int S, cudaStream_t st);
+    // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
+    static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,
+                           const int* child_index, const int* parent_slot, int n_parents,
+                           T* dst, const T* W, cudaStream_t st);
+    // u[slot] += Interp(u_parent[parent]) for each item.
+    static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items,
+                              T* u, const T* up, const T* W, cudaStream_t st);
+};
+
+}  // namespace lgf

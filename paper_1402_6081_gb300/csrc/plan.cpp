@@ -1,0 +1,818 @@
+// Host side of the LGF solver: the C ABI, the tree and lists of Sec. 3.1, the
+// interpolation stencils of Sec. 2.5, the kernel spectra of Step 0 (Eq.
+// precomp), device workspace, and the launch sequence of Steps 1-3.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "lgf_internal.h"
+
+namespace lgf {
+
+// ---------------------------------------------------------------------------
+// status
+
+namespace {
+thread_local std::string g_err;
+}
+lgf_status fail(lgf_status code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+lgf_status ok() { return LGF_OK; }
+
+static lgf_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(LGF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define LGF_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// FFT length along each axis for the interval levels: the smallest supported
+// length >= 2 n_I - 1 that factors into small radices.
+int s_interval(int n_b) { return n_b == 4 ? 10 : n_b == 8 ? 18 : 36; }
+
+// ---------------------------------------------------------------------------
+// Interpolation stencil (Sec. 2.5): child c node i sits at parent coordinate
+// x = c n_b / 2 + i / 2.  A node on a parent node copies it; otherwise the n_max
+// parent nodes nearest x are used (an odd count takes its extra node on the side
+// of the interval centre n_b/2, the lower side at the centre), shifted to stay
+// inside [0, n_I - 1], with Lagrange weights.
+
+std::vector<double> interp_weights(int n_b, int n_max) {
+    const int nI = n_b + 1;
+    std::vector<double> W(size_t(2) * nI * nI, 0.0);
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < nI; ++i) {
+            const int twice = c * n_b + i;   // 2x
+            double* row = &W[(size_t(c) * nI + i) * nI];
+            if (twice % 2 == 0) {
+                row[twice / 2] = 1.0;
+                continue;
+            }
+            const double x = 0.5 * twice;
+            const int k = twice / 2;   // floor(x), x = k + 1/2
+            int lo;
+            if (n_max % 2 == 0) {
+                lo = k - n_max / 2 + 1;
+            } else {
+                const int m = (n_max - 1) / 2;
+                lo = (twice < n_b) ? k - m + 1 : k - m;   // twice < n_b  <=>  x < centre
+            }
+            lo = std::max(0, std::min(lo, nI - n_max));
+            for (int a = lo; a < lo + n_max; ++a) {
+                double w = 1.0;
+                for (int b = lo; b < lo + n_max; ++b)
+                    if (b != a) w *= (x - b) / double(a - b);
+                row[a] = w;
+            }
+        }
+    return W;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel spectra (Step 0): for offset d = idx(Q) - idx(P) at spacing h, the
+// kernel vector k(m) = G(h (m - d n_b)), |m_a| <= n - 1, stored at m mod S and
+// transformed by a 3D real FFT in FP64; 1/S^3 of the inverse transform is
+// folded in.  Level 0 ("near") keeps the 27 offsets |d| <= 1 with n = n_b;
+// interval levels keep all 7^3 offsets |d| <= 3 with n = n_I, zero at the 27
+// near ones (those pairs belong to finer levels).
+
+struct SpecEntry {
+    int device = 0;
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    ~SpecEntry() {
+        if (ptr) {
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(device);
+            cudaFree(ptr);
+            cudaSetDevice(cur);
+        }
+    }
+};
+
+struct SpecKey {
+    int device, n_b, S, h, near, prec;
+    bool operator<(const SpecKey& o) const {
+        return std::tie(device, n_b, S, h, near, prec) < std::tie(o.device, o.n_b, o.S, o.h, o.near, o.prec);
+    }
+};
+
+static void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
+                            std::complex<double>* outw /* NW */) {
+    const int NX = nx_of(S);
+    std::vector<std::complex<double>> C(size_t(S) * S * NX);
+    std::vector<double> k(size_t(S) * S * S, 0.0);
+    const size_t Wt = size_t(V) + 1;
+    for (int mz = -(n - 1); mz <= n - 1; ++mz)
+        for (int my = -(n - 1); my <= n - 1; ++my)
+            for (int mx = -(n - 1); mx <= n - 1; ++mx) {
+                const int vx = std::abs(mx - d[0] * n_b), vy = std::abs(my - d[1] * n_b),
+                          vz = std::abs(mz - d[2] * n_b);
+                const int iz = (mz % S + S) % S, iy = (my % S + S) % S, ix = (mx % S + S) % S;
+                k[(size_t(iz) * S + iy) * S + ix] = tab[(size_t(vx) * Wt + vy) * Wt + vz];
+            }
+    (void)h;
+    // x: real lines -> first NX frequencies
+    std::vector<std::complex<double>> line(S);
+    for (int z = 0; z < S; ++z)
+        for (int y = 0; y < S; ++y) {
+            for (int x = 0; x < S; ++x) line[x] = k[(size_t(z) * S + y) * S + x];
+            fft_lines(line.data(), S, 1, 1, 0, -1);
+            for (int kx = 0; kx < NX; ++kx) C[(size_t(z) * S + y) * NX + kx] = line[kx];
+        }
+    // y: lines (z, kx), stride NX; z: lines (y, kx), stride S*NX
+    for (int z = 0; z < S; ++z) fft_lines(&C[size_t(z) * S * NX], S, NX, NX, 1, -1);
+    fft_lines(C.data(), S, S * NX, S * NX, 1, -1);
+    const double inv = 1.0 / (double(S) * S * S);
+    for (size_t i = 0; i < C.size(); ++i) outw[i] = C[i] * inv;
+}
+
+static std::mutex g_spec_mu;
+static std::map<SpecKey, std::weak_ptr<SpecEntry>> g_spec_cache;
+
+static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int prec,
+                              std::shared_ptr<SpecEntry>& out) {
+    const SpecKey key{device, n_b, S, h, near ? 1 : 0, prec};
+    std::lock_guard<std::mutex> lock(g_spec_mu);
+    auto it = g_spec_cache.find(key);
+    if (it != g_spec_cache.end()) {
+        if (auto sp = it->second.lock()) {
+            out = sp;
+            return ok();
+        }
+    }
+    const int n = near ? n_b : n_b + 1;
+    const int V = near ? 2 * n_b - 1 : 4 * n_b;
+    auto tab = green_abs_table(h, V);
+    const int nd = near ? 27 : 343;
+    const int64_t NW = nw_of(S);
+    std::vector<std::complex<double>> all(size_t(nd) * NW, 0.0);
+    std::vector<int> todo;
+    for (int id = 0; id < nd; ++id) {
+        const int r = near ? 3 : 7, o = near ? 1 : 3;
+        const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
+        const bool is_near = std::abs(d[0]) <= 1 && std::abs(d[1]) <= 1 && std::abs(d[2]) <= 1;
+        if (near || !is_near) todo.push_back(id);
+    }
+    unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nthr; ++w)
+        th.emplace_back([&, w] {
+            for (size_t t = w; t < todo.size(); t += nthr) {
+                const int id = todo[t];
+                const int r = near ? 3 : 7, o = near ? 1 : 3;
+                const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
+                kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(id) * NW]);
+            }
+        });
+    for (auto& t : th) t.join();
+    auto e = std::make_shared<SpecEntry>();
+    e->device = device;
+    const size_t elem = prec == LGF_FP64 ? sizeof(double) : sizeof(float);
+    e->bytes = size_t(nd) * NW * 2 * elem;
+    cudaError_t ce = cudaMalloc(&e->ptr, e->bytes);
+    if (ce != cudaSuccess) {
+        e->ptr = nullptr;
+        return fail(LGF_ERR_OOM, std::string("spectra allocation: ") + cudaGetErrorString(ce));
+    }
+    if (prec == LGF_FP64) {
+        ce = cudaMemcpy(e->ptr, all.data(), e->bytes, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> f(size_t(nd) * NW * 2);
+        for (size_t i = 0; i < all.size(); ++i) {
+            f[2 * i] = float(all[i].real());
+            f[2 * i + 1] = float(all[i].imag());
+        }
+        ce = cudaMemcpy(e->ptr, f.data(), e->bytes, cudaMemcpyHostToDevice);
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "spectra upload");
+    g_spec_cache[key] = e;
+    out = e;
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// Tree (Sec. 3.1): level-1 intervals are the blocks; the level-l index of a
+// block b is floor(b / 2^(l-1)).  Sibling groups: index >> 1; a level's spectra
+// are stored in slots group*8 + child, child = cx + 2 cy + 4 cz.
+
+using I3 = std::array<int, 3>;
+
+static inline int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+static inline I3 parent_of(const I3& a) { return {fdiv2(a[0]), fdiv2(a[1]), fdiv2(a[2])}; }
+static inline int child_of(const I3& a) {
+    return (a[0] - 2 * fdiv2(a[0])) + 2 * (a[1] - 2 * fdiv2(a[1])) + 4 * (a[2] - 2 * fdiv2(a[2]));
+}
+static inline uint64_t pack(const I3& a) {
+    return (uint64_t(uint32_t(a[0] + (1 << 20))) << 42) | (uint64_t(uint32_t(a[1] + (1 << 20))) << 21) |
+           uint64_t(uint32_t(a[2] + (1 << 20)));
+}
+static uint64_t morton(const I3& a, const I3& lo) {
+    uint64_t m = 0;
+    for (int bit = 0; bit < 21; ++bit)
+        for (int ax = 0; ax < 3; ++ax)
+            m |= uint64_t(((a[ax] - lo[ax]) >> bit) & 1) << (3 * bit + ax);
+    return m;
+}
+static inline bool near(const I3& a, const I3& b) {
+    return std::abs(a[0] - b[0]) <= 1 && std::abs(a[1] - b[1]) <= 1 && std::abs(a[2] - b[2]) <= 1;
+}
+
+struct Level {
+    std::vector<I3> iv;                               // intervals (blocks at l = 0, 1)
+    std::unordered_map<uint64_t, int> iv_index;
+    std::vector<I3> groups;                           // Morton-sorted iv >> 1
+    std::unordered_map<uint64_t, int> group_index;
+    bool m2l = false;
+    int slot(const I3& a) const { return group_index.at(pack(parent_of(a))) * 8 + child_of(a); }
+};
+
+struct DevLevel {
+    int n_groups = 0;
+    bool m2l = false;
+    void* fh = nullptr;
+    void* uh = nullptr;
+    void* ft = nullptr;
+    void* ut = nullptr;
+    int* gnbr = nullptr;
+    R2CItem* r2c = nullptr;
+    int n_r2c = 0;
+    C2RItem* c2r = nullptr;
+    int n_c2r = 0;
+    int* reg_child = nullptr;
+    int* reg_parent = nullptr;
+    int n_reg = 0;
+    int* int_slot = nullptr;
+    int* int_parent = nullptr;
+    int n_int = 0;
+    std::shared_ptr<SpecEntry> kh;
+};
+
+}  // namespace lgf
+
+struct lgf_plan_s {
+    int device = 0;
+    int n_b = 0, n_I = 0, L = 0, n_max = 0, prec = LGF_FP32;
+    int64_t n_blocks = 0, n_points = 0;
+    int S0 = 0, SI = 0, Lmac = 0;
+    std::vector<lgf::DevLevel> lev;
+    void* W = nullptr;
+    lgf::C2RItem* out_items = nullptr;
+    int n_out = 0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    void* stage_f = nullptr;
+    void* stage_u = nullptr;
+    // per-kernel event timing (lgf_plan_set_timing / lgf_plan_timings)
+    std::vector<cudaEvent_t> ev;           // 2 * capacity events
+    std::vector<const char*> ev_name;      // kernel name per recorded pair
+    int ev_used = 0;
+    int launches_last = 0;                 // kernels launched by the last solve
+
+    ~lgf_plan_s() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        cudaDeviceSynchronize();
+        for (void* p : allocs) cudaFree(p);
+        if (stage_f) cudaFree(stage_f);
+        if (stage_u) cudaFree(stage_u);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        lev.clear();
+        cudaSetDevice(cur);
+    }
+};
+
+namespace lgf {
+
+static lgf_status dalloc(lgf_plan_s* P, size_t bytes, void** out, bool zero) {
+    *out = nullptr;
+    if (bytes == 0) return ok();
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(LGF_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes: " +
+                                     cudaGetErrorString(e));
+    }
+    P->allocs.push_back(*out);
+    P->bytes += bytes;
+    if (zero) LGF_CUDA(cudaMemset(*out, 0, bytes));
+    return ok();
+}
+
+template <typename V>
+static lgf_status upload(lgf_plan_s* P, const std::vector<V>& h, V** out) {
+    *out = nullptr;
+    if (h.empty()) return ok();
+    void* p = nullptr;
+    lgf_status s = dalloc(P, sizeof(V) * h.size(), &p, false);
+    if (s != LGF_OK) return s;
+    LGF_CUDA(cudaMemcpy(p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+    *out = static_cast<V*>(p);
+    return ok();
+}
+
+static std::mutex g_tw_mu;
+static std::set<std::pair<int, int>> g_tw_done;
+
+static lgf_status ensure_twiddles(int device, int prec) {
+    std::lock_guard<std::mutex> lock(g_tw_mu);
+    if (g_tw_done.count({device, prec})) return ok();
+    cudaError_t e = prec == LGF_FP64 ? Launch<double>::init_twiddles() : Launch<float>::init_twiddles();
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle upload");
+    g_tw_done.insert({device, prec});
+    return ok();
+}
+
+static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
+    const int nb = P->n_b, nI = P->n_I, L = P->L;
+    const int64_t NB = P->n_blocks;
+    std::vector<I3> blocks(static_cast<size_t>(NB));
+    std::unordered_map<uint64_t, int> bidx;
+    for (int64_t b = 0; b < NB; ++b) {
+        I3 v{ijk[3 * b], ijk[3 * b + 1], ijk[3 * b + 2]};
+        for (int a = 0; a < 3; ++a)
+            if (std::abs(v[a]) > (1 << 19)) return fail(LGF_ERR_INVALID_ARG, "block index out of range (|i| > 2^19)");
+        if (!bidx.emplace(pack(v), int(b)).second)
+            return fail(LGF_ERR_INVALID_ARG, "duplicate block in block_ijk at position " + std::to_string(b));
+        blocks[size_t(b)] = v;
+    }
+    // levels 0..L: level 0 and 1 are the blocks
+    std::vector<Level> lv(static_cast<size_t>(L) + 1);
+    lv[0].iv = blocks;
+    for (int l = 1; l <= L; ++l) {
+        if (l == 1) {
+            lv[1].iv = blocks;
+        } else {
+            std::unordered_set<uint64_t> seen;
+            for (const I3& a : lv[size_t(l) - 1].iv) {
+                I3 p = parent_of(a);
+                if (seen.insert(pack(p)).second) lv[size_t(l)].iv.push_back(p);
+            }
+        }
+        auto& L_ = lv[size_t(l)];
+        for (size_t i = 0; i < L_.iv.size(); ++i) L_.iv_index[pack(L_.iv[i])] = int(i);
+    }
+    lv[0].iv_index = lv[1].iv_index;
+    // the root level must have no interaction list
+    {
+        I3 lo = lv[size_t(L)].iv[0], hi = lo;
+        for (const I3& a : lv[size_t(L)].iv)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], a[k]);
+                hi[k] = std::max(hi[k], a[k]);
+            }
+        if (hi[0] - lo[0] > 1 || hi[1] - lo[1] > 1 || hi[2] - lo[2] > 1) {
+            int need = L;
+            for (int l = L + 1; l < 40; ++l) {
+                I3 a, b;
+                for (int k = 0; k < 3; ++k) {
+                    a[k] = lo[k];
+                    b[k] = hi[k];
+                    for (int s = L; s < l; ++s) {
+                        a[k] = fdiv2(a[k]);
+                        b[k] = fdiv2(b[k]);
+                    }
+                }
+                if (b[0] - a[0] <= 1 && b[1] - a[1] <= 1 && b[2] - a[2] <= 1) {
+                    need = l;
+                    break;
+                }
+            }
+            return fail(LGF_ERR_UNSUPPORTED,
+                        "n_levels=" + std::to_string(L) + " leaves intervals at the root level that are not "
+                        "mutually near (the root level would need its own interaction list); use n_levels >= " +
+                            std::to_string(need));
+        }
+    }
+    // interaction lists: does level l (1 <= l < L) have any?
+    int Lmac = 0;
+    for (int l = 1; l < L; ++l) {
+        const auto& L_ = lv[size_t(l)];
+        bool any = false;
+        for (const I3& a : L_.iv) {
+            const I3 pp = parent_of(a);
+            for (int e = 0; e < 216 && !any; ++e) {
+                const int cx = e & 1, cy = (e >> 1) & 1, cz = (e >> 2) & 1, ee = e >> 3;
+                const I3 q{2 * (pp[0] + ee % 3 - 1) + cx, 2 * (pp[1] + (ee / 3) % 3 - 1) + cy,
+                           2 * (pp[2] + ee / 9 - 1) + cz};
+                if (!near(a, q) && L_.iv_index.count(pack(q))) any = true;
+            }
+            if (any) break;
+        }
+        lv[size_t(l)].m2l = any;
+        if (any) Lmac = l;
+    }
+    P->Lmac = Lmac;
+    // sibling groups and slots for levels 0..Lmac
+    for (int l = 0; l <= Lmac; ++l) {
+        auto& L_ = lv[size_t(l)];
+        std::unordered_set<uint64_t> seen;
+        for (const I3& a : L_.iv) {
+            I3 g = parent_of(a);
+            if (seen.insert(pack(g)).second) L_.groups.push_back(g);
+        }
+        I3 lo = L_.groups[0];
+        for (const I3& g : L_.groups)
+            for (int k = 0; k < 3; ++k) lo[k] = std::min(lo[k], g[k]);
+        std::sort(L_.groups.begin(), L_.groups.end(),
+                  [&](const I3& a, const I3& b) { return morton(a, lo) < morton(b, lo); });
+        for (size_t i = 0; i < L_.groups.size(); ++i) L_.group_index[pack(L_.groups[i])] = int(i);
+    }
+    // ---- device objects ----
+    const size_t elem = P->prec == LGF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t cplx = 2 * elem;
+    const size_t n3 = size_t(nI) * nI * nI;
+    P->lev.resize(size_t(Lmac) + 1);
+    for (int l = 0; l <= Lmac; ++l) {
+        const auto& L_ = lv[size_t(l)];
+        DevLevel& D = P->lev[size_t(l)];
+        D.n_groups = int(L_.groups.size());
+        D.m2l = (l == 0) || L_.m2l;
+        const size_t slots = size_t(D.n_groups) * 8;
+        lgf_status s;
+        if (D.m2l) {
+            const int S = l == 0 ? P->S0 : P->SI;
+            const size_t NW = size_t(nw_of(S));
+            if ((s = dalloc(P, slots * NW * cplx, &D.fh, true)) != LGF_OK) return s;
+            if ((s = dalloc(P, slots * NW * cplx, &D.uh, false)) != LGF_OK) return s;
+            std::vector<int> gn(size_t(D.n_groups) * 27, -1);
+            for (int g = 0; g < D.n_groups; ++g)
+                for (int e = 0; e < 27; ++e) {
+                    const I3& G = L_.groups[size_t(g)];
+                    I3 q{G[0] + e % 3 - 1, G[1] + (e / 3) % 3 - 1, G[2] + e / 9 - 1};
+                    auto it = L_.group_index.find(pack(q));
+                    if (it != L_.group_index.end()) gn[size_t(g) * 27 + e] = it->second;
+                }
+            if ((s = upload(P, gn, &D.gnbr)) != LGF_OK) return s;
+            std::vector<R2CItem> items;
+            for (size_t i = 0; i < L_.iv.size(); ++i) {
+                const int slot = L_.slot(L_.iv[i]);
+                items.push_back({l <= 1 ? int(i) : slot, slot});
+            }
+            D.n_r2c = int(items.size());
+            if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
+            const int h = l == 0 ? 1 : (1 << (l - 1));
+            if ((s = get_spectra(P->device, nb, S, h, l == 0, P->prec, D.kh)) != LGF_OK) return s;
+        }
+        if (l >= 1) {
+            if ((s = dalloc(P, slots * n3 * elem, &D.ut, true)) != LGF_OK) return s;
+            if (D.m2l) {
+                std::vector<C2RItem> items;
+                for (const I3& a : L_.iv) {
+                    const int slot = L_.slot(a);
+                    items.push_back({slot, slot, -1});
+                }
+                D.n_c2r = int(items.size());
+                if ((s = upload(P, items, &D.c2r)) != LGF_OK) return s;
+            }
+        }
+        if (l >= 2) {
+            if ((s = dalloc(P, slots * n3 * elem, &D.ft, true)) != LGF_OK) return s;
+            const auto& Lc = lv[size_t(l) - 1];
+            std::vector<int> child, par;
+            for (const I3& a : L_.iv) {
+                par.push_back(L_.slot(a));
+                const int cg = Lc.group_index.at(pack(a));
+                for (int c = 0; c < 8; ++c) {
+                    const I3 q{2 * a[0] + (c & 1), 2 * a[1] + ((c >> 1) & 1), 2 * a[2] + (c >> 2)};
+                    auto it = Lc.iv_index.find(pack(q));
+                    if (it == Lc.iv_index.end()) child.push_back(-1);
+                    else child.push_back(l == 2 ? it->second : cg * 8 + c);
+                }
+            }
+            D.n_reg = int(par.size());
+            if ((s = upload(P, child, &D.reg_child)) != LGF_OK) return s;
+            if ((s = upload(P, par, &D.reg_parent)) != LGF_OK) return s;
+        }
+        if (l >= 1 && l < Lmac) {
+            const auto& Lp = lv[size_t(l) + 1];
+            std::vector<int> sl, pa;
+            for (const I3& a : L_.iv) {
+                sl.push_back(L_.slot(a));
+                pa.push_back(Lp.slot(parent_of(a)));
+            }
+            D.n_int = int(sl.size());
+            if ((s = upload(P, sl, &D.int_slot)) != LGF_OK) return s;
+            if ((s = upload(P, pa, &D.int_parent)) != LGF_OK) return s;
+        }
+    }
+    // level-0 output items: block b from its level-0 slot, plus level-1 field
+    {
+        std::vector<C2RItem> items;
+        for (int64_t b = 0; b < NB; ++b) {
+            const int slot = lv[0].slot(blocks[size_t(b)]);
+            items.push_back({slot, int(b), Lmac >= 1 ? slot : -1});
+        }
+        P->n_out = int(items.size());
+        lgf_status s = upload(P, items, &P->out_items);
+        if (s != LGF_OK) return s;
+    }
+    // interpolation weights in the plan precision
+    {
+        std::vector<double> W = interp_weights(nb, P->n_max);
+        lgf_status s;
+        if (P->prec == LGF_FP64) {
+            double* d = nullptr;
+            if ((s = upload(P, W, &d)) != LGF_OK) return s;
+            P->W = d;
+        } else {
+            std::vector<float> wf(W.begin(), W.end());
+            float* d = nullptr;
+            if ((s = upload(P, wf, &d)) != LGF_OK) return s;
+            P->W = d;
+        }
+    }
+    return ok();
+}
+
+// Runs one launch; with timing enabled, brackets it by an event pair on `st`.
+template <typename F>
+static cudaError_t timed(lgf_plan_s* P, const char* name, cudaStream_t st, F&& launch) {
+    ++P->launches_last;
+    const int k = P->ev_used;
+    const bool rec = 2 * (k + 1) <= int(P->ev.size());
+    if (rec) cudaEventRecord(P->ev[size_t(2 * k)], st);
+    cudaError_t e = launch();
+    if (rec) {
+        cudaEventRecord(P->ev[size_t(2 * k + 1)], st);
+        P->ev_name[size_t(k)] = name;
+        P->ev_used = k + 1;
+    }
+    return e;
+}
+
+template <typename T>
+static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
+    using Lc = Launch<T>;
+    P->launches_last = 0;
+    const int nb = P->n_b, nI = P->n_I;
+    const int64_t n3 = int64_t(nI) * nI * nI, b3 = int64_t(nb) * nb * nb;
+    auto& lev = P->lev;
+    const T* W = static_cast<const T*>(P->W);
+    cudaError_t e;
+    // Step 1: upward pass
+    e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
+    for (int l = 1; l <= P->Lmac; ++l) {
+        DevLevel& D = lev[size_t(l)];
+        if (l >= 2) {
+            const bool from_blocks = l == 2;
+            e = timed(P, "reg", st, [&] {
+                return Lc::reg(nb, P->n_max, from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft),
+                               from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg, static_cast<T*>(D.ft), W, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "regularization");
+        }
+        if (D.m2l) {
+            e = timed(P, "r2c_interval", st, [&] {
+                return l == 1 ? Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, st)
+                              : Lc::r2c(P->SI, nI, static_cast<const T*>(D.ft), n3, D.r2c, D.n_r2c, D.fh, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
+        }
+    }
+    // Step 2: level interactions
+    e = timed(P, "mac_level0", st, [&] {
+        return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "near-field products");
+    for (int l = 1; l <= P->Lmac; ++l) {
+        DevLevel& D = lev[size_t(l)];
+        if (!D.m2l) continue;
+        e = timed(P, l == 1 ? "mac_interval_l1" : "mac_interval_l2plus", st, [&] {
+            return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
+    }
+    // Step 3: downward pass
+    for (int l = P->Lmac; l >= 1; --l) {
+        DevLevel& D = lev[size_t(l)];
+        if (D.m2l) {
+            e = timed(P, "c2r_interval", st, [&] {
+                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
+        } else {
+            e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), st);
+            if (e != cudaSuccess) return cuda_fail(e, "clear level field");
+        }
+        if (l < P->Lmac) {
+            e = timed(P, "interp", st, [&] {
+                return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
+                                  static_cast<const T*>(lev[size_t(l) + 1].ut), W, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+        }
+    }
+    const T* add = P->Lmac >= 1 ? static_cast<const T*>(lev[1].ut) : nullptr;
+    e = timed(P, "c2r_level0", st, [&] {
+        return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "level-0 inverse FFT");
+    return ok();
+}
+
+static lgf_status check_device(const lgf_plan_s* P) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != P->device)
+        return fail(LGF_ERR_INVALID_ARG, "plan belongs to device " + std::to_string(P->device) +
+                                             " but device " + std::to_string(cur) + " is current");
+    return ok();
+}
+
+}  // namespace lgf
+
+using namespace lgf;
+
+extern "C" {
+
+const char* lgf_last_error(void) { return g_err.c_str(); }
+
+lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double* W) {
+    if (!W || n_b < 2 || n_max < 1 || n_max > n_b + 1)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_interp_weights: need W != NULL, n_b >= 2, 1 <= n_max <= n_b + 1");
+    std::vector<double> v = interp_weights(n_b, n_max);
+    std::memcpy(W, v.data(), sizeof(double) * v.size());
+    return ok();
+}
+
+lgf_status lgf_plan_create(const int32_t* block_ijk, int64_t n_blocks, int32_t n_b, int32_t n_levels,
+                           int32_t interp_order, int32_t precision, int32_t interp_mode, lgf_plan* out) {
+    if (!out) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: out is NULL");
+    *out = nullptr;
+    if (!block_ijk || n_blocks < 1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need n_blocks >= 1 block indices");
+    if (n_blocks > (int64_t(1) << 26)) return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: more than 2^26 blocks");
+    if (n_b != 4 && n_b != 8 && n_b != 16)
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: n_b must be 4, 8 or 16");
+    if (n_levels < 1 || n_levels > 24) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 1 <= n_levels <= 24");
+    if (interp_order < 0 || interp_order + 1 > n_b + 1)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
+    if (precision != LGF_FP32 && precision != LGF_FP64)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: precision must be LGF_FP32 or LGF_FP64");
+    if (interp_mode != LGF_INTERP_NATIVE)
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: interp_mode must be LGF_INTERP_NATIVE");
+    auto P = std::make_unique<lgf_plan_s>();
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    P->n_b = n_b;
+    P->n_I = n_b + 1;
+    P->L = n_levels;
+    P->n_max = interp_order + 1;
+    P->prec = precision;
+    P->n_blocks = n_blocks;
+    P->n_points = n_blocks * int64_t(n_b) * n_b * n_b;
+    P->S0 = s_level0(n_b);
+    P->SI = s_interval(n_b);
+    lgf_status s = ensure_twiddles(P->device, precision);
+    if (s != LGF_OK) return s;
+    s = build_plan(P.get(), block_ijk);
+    if (s != LGF_OK) return s;
+    *out = P.release();
+    return ok();
+}
+
+lgf_status lgf_plan_workspace_bytes(lgf_plan plan, size_t* bytes) {
+    if (!plan || !bytes) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_workspace_bytes: NULL argument");
+    size_t b = plan->bytes;
+    for (auto& D : plan->lev)
+        if (D.kh) b += D.kh->bytes;
+    *bytes = b;
+    return ok();
+}
+
+lgf_status lgf_plan_points(lgf_plan plan, int64_t* n_points) {
+    if (!plan || !n_points) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_points: NULL argument");
+    *n_points = plan->n_points;
+    return ok();
+}
+
+lgf_status lgf_solve(lgf_plan plan, const void* f_dev, void* u_dev, void* stream) {
+    if (!plan || !f_dev || !u_dev) return fail(LGF_ERR_INVALID_ARG, "lgf_solve: NULL argument");
+    if (f_dev == u_dev) return fail(LGF_ERR_INVALID_ARG, "lgf_solve: f and u must not overlap");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plan->prec == LGF_FP64)
+        return solve_impl<double>(plan, static_cast<const double*>(f_dev), static_cast<double*>(u_dev), st);
+    return solve_impl<float>(plan, static_cast<const float*>(f_dev), static_cast<float*>(u_dev), st);
+}
+
+lgf_status lgf_solve_batch(const lgf_plan* plans, const void* const* f_dev, void* const* u_dev, int32_t n,
+                           void* stream) {
+    if (n < 0 || (n > 0 && (!plans || !f_dev || !u_dev)))
+        return fail(LGF_ERR_INVALID_ARG, "lgf_solve_batch: bad arguments");
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < i; ++j)
+            if (plans[i] == plans[j]) return fail(LGF_ERR_INVALID_ARG, "lgf_solve_batch: plans must be distinct");
+    for (int32_t i = 0; i < n; ++i) {
+        lgf_status s = lgf_solve(plans[i], f_dev[i], u_dev[i], stream);
+        if (s != LGF_OK) return s;
+    }
+    return ok();
+}
+
+lgf_status lgf_solve_host(lgf_plan plan, const void* f_host, void* u_host, void* stream) {
+    if (!plan || !f_host || !u_host) return fail(LGF_ERR_INVALID_ARG, "lgf_solve_host: NULL argument");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    const size_t bytes = size_t(plan->n_points) * (plan->prec == LGF_FP64 ? sizeof(double) : sizeof(float));
+    if (!plan->stage_f) {
+        cudaError_t e = cudaMalloc(&plan->stage_f, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->stage_u, bytes);
+        if (e != cudaSuccess) return fail(LGF_ERR_OOM, std::string("staging buffers: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LGF_CUDA(cudaMemcpyAsync(plan->stage_f, f_host, bytes, cudaMemcpyHostToDevice, st));
+    s = lgf_solve(plan, plan->stage_f, plan->stage_u, stream);
+    if (s != LGF_OK) return s;
+    LGF_CUDA(cudaMemcpyAsync(u_host, plan->stage_u, bytes, cudaMemcpyDeviceToHost, st));
+    LGF_CUDA(cudaStreamSynchronize(st));
+    return ok();
+}
+
+lgf_status lgf_plan_set_timing(lgf_plan plan, int32_t capacity) {
+    if (!plan || capacity < 0 || capacity > (1 << 16))
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_set_timing: need a plan and 0 <= capacity <= 65536");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    LGF_CUDA(cudaDeviceSynchronize());
+    for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
+    plan->ev.clear();
+    plan->ev_name.assign(size_t(capacity), nullptr);
+    plan->ev_used = 0;
+    for (int i = 0; i < 2 * capacity; ++i) {
+        cudaEvent_t e;
+        LGF_CUDA(cudaEventCreate(&e));
+        plan->ev.push_back(e);
+    }
+    return ok();
+}
+
+lgf_status lgf_plan_timings(lgf_plan plan, int32_t max_kernels, int32_t* n_kernels, char* names,
+                            double* total_ms, int32_t* count, int32_t* launches_per_solve) {
+    if (!plan || !n_kernels || max_kernels < 0 || (max_kernels > 0 && (!names || !total_ms || !count)))
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_timings: bad arguments");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    std::vector<std::string> nm;
+    std::vector<double> tot;
+    std::vector<int> cnt;
+    for (int k = 0; k < plan->ev_used; ++k) {
+        LGF_CUDA(cudaEventSynchronize(plan->ev[size_t(2 * k + 1)]));
+        float ms = 0.f;
+        LGF_CUDA(cudaEventElapsedTime(&ms, plan->ev[size_t(2 * k)], plan->ev[size_t(2 * k + 1)]));
+        const std::string name = plan->ev_name[size_t(k)];
+        size_t j = 0;
+        while (j < nm.size() && nm[j] != name) ++j;
+        if (j == nm.size()) {
+            nm.push_back(name);
+            tot.push_back(0.0);
+            cnt.push_back(0);
+        }
+        tot[j] += ms;
+        cnt[j] += 1;
+    }
+    *n_kernels = int32_t(nm.size());
+    for (size_t j = 0; j < nm.size() && int32_t(j) < max_kernels; ++j) {
+        std::memset(names + 32 * j, 0, 32);
+        std::strncpy(names + 32 * j, nm[j].c_str(), 31);
+        total_ms[j] = tot[j];
+        count[j] = cnt[j];
+    }
+    if (launches_per_solve) *launches_per_solve = plan->launches_last;
+    plan->ev_used = 0;
+    return ok();
+}
+
+lgf_status lgf_plan_sync(lgf_plan plan) {
+    if (!plan) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_sync: NULL plan");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    LGF_CUDA(cudaDeviceSynchronize());
+    return ok();
+}
+
+lgf_status lgf_destroy(lgf_plan plan) {
+    if (!plan) return fail(LGF_ERR_INVALID_ARG, "lgf_destroy: NULL plan");
+    delete plan;
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Tolerances (relative L-infinity over the active points, max|u - ref| / max|ref|):
+  * FP64 path vs the FP64 oracle FMM: 1e-12 (both compute the same truncated
+    method; only rounding differs, and FP64 rounding over a few hundred spectral
+    products and three FFT passes stays near 1e-15).
+  * FP32 path vs the FP64 oracle FMM: 1e-5 (FP32 rounding of inputs, spectra,
+    FFTs and up to 216 products per frequency: ~1e-6 expected).
+Where the method involves no interpolation the oracle FMM itself equals the
+exact direct sum, so the same bounds hold against it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1402_6081_gb300 as lgfm
+import workloads as W
+from oracle import direct, fmm
+from paper_1402_6081_gb300 import build as lgf_build
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lgf_build.build()
+    lgfm.library()
+
+
+_oracle_cache = {}
+
+
+def oracle_u(p):
+    key = (p.name, p.n_b, p.n_levels, p.order, len(p.blocks), float(np.abs(p.f).sum()))
+    if key not in _oracle_cache:
+        _oracle_cache[key] = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order)
+    return _oracle_cache[key]
+
+
+def gpu_solve(p, prec, f=None):
+    dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec)
+    ft = torch.from_numpy(np.ascontiguousarray(p.f if f is None else f)).to(dt).cuda()
+    u = s(ft)
+    torch.cuda.synchronize()
+    out = u.double().cpu().numpy()
+    s.close()
+    return out
+
+
+def check(p, tol64=TOL64, tol32=TOL32):
+    ref = oracle_u(p)
+    e64 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ref)
+    e32 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ref)
+    assert e64 <= tol64, ("fp64", e64)
+    assert e32 <= tol32, ("fp32", e32)
+    return e64, e32
+
+
+def test_gaussian_32_two_levels_vs_direct_sum():
+    # 32^3 Gaussian, 4^3 blocks of 8^3, two levels, order 6: exact method
+    p = W.config(0)
+    ud = direct.direct_sum(p.blocks, p.n_b, p.f)
+    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ud) <= TOL64
+    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ud) <= TOL32
+    check(p)
+
+
+def test_torus_128_three_levels():
+    # the single-solve workload: 128^3, 8^3 blocks of 16^3, 3 levels, order 8
+    p = W.config(1)
+    check(p)
+
+
+@pytest.mark.parametrize("n_b", [4, 8, 16])
+def test_single_block_is_fft_convolution(n_b):
+    rng = np.random.default_rng(n_b)
+    blocks = np.array([[-3, 2, 7]], dtype=np.int32)
+    f = rng.standard_normal((1, n_b, n_b, n_b))
+    p = W.Problem(blocks, f, n_b, 1, min(n_b, 8), f"single{n_b}")
+    ud = direct.direct_sum(blocks, n_b, f)
+    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ud) <= TOL64
+    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ud) <= TOL32
+
+
+def test_manufactured_three_levels_nb8():
+    # interpolation active at level 2; the answer is known exactly (Sec. 4.1)
+    m = W.manufactured(W.full_box_blocks(8), 8, 3, 8, seed=0)
+    e64, e32 = check(m)
+    err_gpu = fmm.rel_linf(gpu_solve(m, lgfm.LGF_FP64), m.u_exact)
+    err_orc = fmm.rel_linf(oracle_u(m), m.u_exact)
+    assert abs(err_gpu - err_orc) <= 1e-12 and 1e-9 < err_orc < 1e-5
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_irregular_sparse_nb4(order):
+    # half of an 8^3 block grid, shifted to negative indices; 4 levels; the
+    # ragged sibling groups leave holes in every level
+    rng = np.random.default_rng(21 + order)
+    allb = W.full_box_blocks(8) - np.array([5, 3, 6], dtype=np.int32)
+    keep = rng.uniform(size=len(allb)) < 0.5
+    blocks = allb[keep]
+    f = rng.uniform(-1, 1, size=(len(blocks), 4, 4, 4))
+    p = W.Problem(blocks, f, 4, 4, order, f"sparse_nb4_o{order}")
+    check(p)
+
+
+def test_far_blocks_only_upper_level_interacts():
+    # level 1 has no interaction list; level 2 does
+    blocks = np.array([[0, 0, 0], [5, 0, 0], [5, 1, 0], [0, 1, 1]], dtype=np.int32)
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((4, 8, 8, 8))
+    p = W.Problem(blocks, f, 8, 4, 6, "far_pairs")
+    check(p)
+
+
+def test_deep_tree_nb4_five_levels():
+    m = W.manufactured(W.full_box_blocks(16, 8, 8), 4, 5, 4, seed=3)
+    check(m)
+
+
+def test_plan_errors():
+    b = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0]], dtype=np.int32)
+    with pytest.raises(lgfm.LgfError) as e:
+        lgfm.lgf_plan_create(b, 8, 2, 6, lgfm.LGF_FP32)
+    assert e.value.status == 1 and "duplicate" in str(e.value)
+    with pytest.raises(lgfm.LgfError) as e:
+        lgfm.lgf_plan_create(W.full_box_blocks(8), 8, 2, 6, lgfm.LGF_FP32)
+    assert e.value.status == 2 and "n_levels >= 3" in str(e.value)
+    with pytest.raises(lgfm.LgfError) as e:
+        lgfm.lgf_plan_create(W.full_box_blocks(2), 6, 1, 4, lgfm.LGF_FP32)
+    assert e.value.status == 2
+    with pytest.raises(lgfm.LgfError) as e:
+        lgfm.lgf_plan_create(W.full_box_blocks(2), 8, 1, 9, lgfm.LGF_FP32)
+    assert e.value.status == 1
+
+
+def test_deterministic_and_host_and_batch_paths():
+    p = W.torus_box(seed=5, nb=4, n_b=8, radius=10.0, sigma=3.0)
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    f = torch.from_numpy(p.f).float().cuda()
+    u1 = s(f).clone()
+    u2 = s(f).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(u1, u2)
+    fh = f.cpu().pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    lgfm.lgf_solve_host(s.plan, fh, uh)
+    assert torch.equal(uh, u1.cpu())
+    s2 = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    ua, ub = torch.empty_like(f), torch.empty_like(f)
+    lgfm.lgf_solve_batch([s.plan, s2.plan], [f, f * 2], [ua, ub])
+    torch.cuda.synchronize()
+    assert torch.equal(ua, u1)
+    assert torch.allclose(ub, 2 * u1, rtol=0, atol=1e-6 * float(u1.abs().max()))
+    s.close()
+    s2.close()
+
+
+def test_timing_api_counts_launches():
+    p = W.config(1)
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    f = torch.from_numpy(p.f).float().cuda()
+    lgfm.lgf_plan_set_timing(s.plan, 64)
+    s(f)
+    s(f)
+    t, per = lgfm.lgf_plan_timings(s.plan)
+    # 128^3, 3 levels: r2c x3, reg, mac x3, c2r x3, interp
+    assert per == 11
+    assert t["mac_interval_l1"][1] == 2 and t["mac_interval_l1"][0] > 0
+    assert sum(c for _, c in t.values()) == 22
+    s.close()
+
+
+# ---- full-size irregular workload: properties that hold at any size ----
+
+@pytest.fixture(scope="module")
+def irregular():
+    return W.tori_irregular(2)
+
+
+def test_irregular_512_fp32_vs_fp64(irregular):
+    p = irregular
+    u64 = gpu_solve(p, lgfm.LGF_FP64)
+    u32 = gpu_solve(p, lgfm.LGF_FP32)
+    assert fmm.rel_linf(u32, u64) <= 2e-6
+    # sampled exact sums: u at a few points equals the direct lattice sum up to
+    # the method's truncation error at this order (n_I = 17, n_max = 9)
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(p.blocks), size=3, replace=False)
+    pts = direct.point_coords(p.blocks[pick], p.n_b)[::97]
+    ud = direct.direct_sum(p.blocks, p.n_b, p.f, targets=pts)
+    idx = [(b, (q % p.n_b ** 3)) for b in pick for q in range(0, p.n_b ** 3)]
+    got = np.array([u64[b].reshape(-1)[q] for b, q in idx])[::97]
+    assert np.abs(got - ud).max() / np.abs(u64).max() < 1e-7
+
+
+def test_irregular_512_manufactured(irregular):
+    m = W.manufactured(irregular.blocks, 16, 5, 8, seed=7)
+    err = fmm.rel_linf(gpu_solve(m, lgfm.LGF_FP64), m.u_exact)
+    assert err < 1e-7
+    err32 = fmm.rel_linf(gpu_solve(m, lgfm.LGF_FP32), m.u_exact)
+    assert err32 < 1e-5
