@@ -62,11 +62,21 @@ def _expansion_coeffs(k: int, nterms: int) -> np.ndarray:
 
 def _tail(triple, alpha: float) -> float:
     """int_alpha^inf prod_i Ie_{n_i}(2t) dt from the term-by-term integral."""
-    c = np.array([1.0])
-    for k in triple:
-        c = np.convolve(c, _expansion_coeffs(int(k), TAIL_TERMS))[: TAIL_TERMS + 1]
-    J = np.arange(TAIL_TERMS + 1)
-    return float((4.0 * math.pi) ** -1.5 * np.sum(c * alpha ** (-0.5 - J) / (J + 0.5)))
+    return float(_tail_many(np.asarray([triple]), np.asarray([alpha]))[0])
+
+
+def _tail_many(trip: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """_tail for many triples at once: the product of the three expansions is
+    truncated after TAIL_TERMS and integrated term by term."""
+    J = TAIL_TERMS
+    b = [np.stack([_expansion_coeffs(int(k), J) for k in range(int(trip.max()) + 1)])[trip[:, i]]
+         for i in range(3)]                                   # (m, J+1) each
+    c = np.zeros((len(trip), J + 1))
+    for i in range(J + 1):
+        for j in range(J + 1 - i):
+            c[:, i + j:] += (b[0][:, i] * b[1][:, j])[:, None] * b[2][:, : J + 1 - i - j]
+    jj = np.arange(J + 1)
+    return (4.0 * math.pi) ** -1.5 * np.sum(c * alpha[:, None] ** (-0.5 - jj) / (jj + 0.5), axis=1)
 
 
 def _panels(max_exp: int, q: int):
@@ -99,10 +109,7 @@ def _lgf_sorted(trip: np.ndarray, q: int = PANEL_NODES) -> np.ndarray:
             tr = trip[idx]
             prod = bes[tr[:, 0], :nq] * bes[tr[:, 1], :nq] * bes[tr[:, 2], :nq]
             out[idx] = prod @ wq
-        alpha = 2.0 ** ae
-        # The tail depends only on the multiset of orders and alpha.
-        for i in sel:
-            out[i] += _tail(trip[i], alpha)
+        out[sel] += _tail_many(trip[sel], np.full(len(sel), 2.0 ** ae))
     return -out
 
 
