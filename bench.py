@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -257,6 +259,13 @@ def main():
         s32(f32, u32, stream)
     torch.cuda.synchronize()
     per_solve_launches = None
+    if args.profile_only:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup + args.steps):
+                s32(f32, u32, stream)
+        torch.cuda.synchronize()
+        s32.close()
+        return
 
     clocks = ClockSampler(dev)
     clocks.start()
