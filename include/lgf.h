@@ -87,6 +87,44 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
                            int32_t n_levels, int32_t interp_order, int32_t precision,
                            int32_t interp_mode, lgf_plan *out);
 
+/*
+ * Tuning options (zero-initialise for the defaults).
+ *   fft_size_interval  FFT length per axis S_I at levels >= 1 (Sec. 2.2: any
+ *                      S_I >= 2 n_I - 1 gives the same linear convolution).
+ *                      0 = default.  Supported: n_b = 4: 10; n_b = 8: 17, 18;
+ *                      n_b = 16: 33, 34, 36.  The level-0 length is 2 n_b.
+ */
+typedef struct {
+    int32_t fft_size_interval;
+    int32_t reserved[15];
+} lgf_plan_options;
+
+/* lgf_plan_create with options (NULL = defaults). */
+lgf_status lgf_plan_create_ex(const int32_t *block_ijk, int64_t n_blocks, int32_t n_b,
+                              int32_t n_levels, int32_t interp_order, int32_t precision,
+                              int32_t interp_mode, const lgf_plan_options *opts, lgf_plan *out);
+
+/*
+ * Plan statistics: the work of one solve (Sec. 3.2 counts for this block set).
+ *   pairs[l]   level 0: near (block, block) pairs; level l >= 1: interaction-list
+ *              (target, source) interval pairs; each costs NW complex products
+ *   intervals[l], groups[l]   intervals and sibling groups per level
+ *   nw[l]      frequencies per spectrum at level l (0 where l has no products)
+ *   top_product_level  highest level with a non-empty interaction list
+ */
+#define LGF_MAX_LEVELS 24
+typedef struct {
+    int64_t n_points, n_blocks;
+    int32_t n_levels, top_product_level, fft_size_level0, fft_size_interval;
+    int64_t pairs[LGF_MAX_LEVELS + 1];
+    int64_t intervals[LGF_MAX_LEVELS + 1];
+    int64_t groups[LGF_MAX_LEVELS + 1];
+    int64_t nw[LGF_MAX_LEVELS + 1];
+    int64_t workspace_bytes;
+} lgf_plan_stats;
+
+lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);
+
 /* Device bytes the plan holds (workspace plus its share of cached spectra);
  * what a serving loop charges against its HBM budget. */
 lgf_status lgf_plan_workspace_bytes(lgf_plan plan, size_t *bytes);

@@ -29,6 +29,10 @@ _SIGS = {
     "lgf_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_plan_create_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_plan_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "lgf_plan_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "lgf_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -95,6 +99,24 @@ def lgf_last_error() -> str:
     return library().lgf_last_error().decode()
 
 
+MAX_LEVELS = 24
+
+
+class lgf_plan_options(ctypes.Structure):
+    _fields_ = [("fft_size_interval", ctypes.c_int32), ("reserved", ctypes.c_int32 * 15)]
+
+
+class lgf_plan_stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_blocks", ctypes.c_int64),
+                ("n_levels", ctypes.c_int32), ("top_product_level", ctypes.c_int32),
+                ("fft_size_level0", ctypes.c_int32), ("fft_size_interval", ctypes.c_int32),
+                ("pairs", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("intervals", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("groups", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
                     precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE) -> int:
     """Plan for the block list ``blocks`` ((n, 3) block indices); returns the handle."""
@@ -103,6 +125,31 @@ def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
     _check(library().lgf_plan_create(b.ctypes.data, len(b), n_b, n_levels, interp_order,
                                      precision, interp_mode, ctypes.byref(out)), "lgf_plan_create")
     return out.value
+
+
+def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
+                       precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
+                       fft_size_interval: int = 0) -> int:
+    """lgf_plan_create with tuning options (0 = default)."""
+    b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
+    opts = lgf_plan_options()
+    opts.fft_size_interval = fft_size_interval
+    out = ctypes.c_void_p()
+    _check(library().lgf_plan_create_ex(b.ctypes.data, len(b), n_b, n_levels, interp_order, precision,
+                                        interp_mode, ctypes.byref(opts), ctypes.byref(out)),
+           "lgf_plan_create_ex")
+    return out.value
+
+
+def lgf_plan_get_stats(plan: int) -> dict:
+    st = lgf_plan_stats()
+    _check(library().lgf_plan_get_stats(plan, ctypes.byref(st)), "lgf_plan_get_stats")
+    L = st.n_levels
+    return {"n_points": st.n_points, "n_blocks": st.n_blocks, "n_levels": L,
+            "top_product_level": st.top_product_level, "fft_size_level0": st.fft_size_level0,
+            "fft_size_interval": st.fft_size_interval, "pairs": list(st.pairs[: L + 1]),
+            "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
+            "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:
@@ -186,11 +233,13 @@ class Solver:
     """Owns one plan: ``Solver(blocks, n_b, n_levels, order, precision)(f) -> u``
     with f, u torch CUDA tensors of shape (n_blocks, n_b, n_b, n_b)."""
 
-    def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32):
+    def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
+                 fft_size_interval: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
-        self.plan = lgf_plan_create(blocks, n_b, n_levels, interp_order, precision)
+        self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision,
+                                       fft_size_interval=fft_size_interval)
 
     @property
     def dtype(self):
@@ -207,6 +256,9 @@ class Solver:
             raise ValueError("f/u size does not match the plan")
         lgf_solve(self.plan, f, u, stream)
         return u
+
+    def stats(self) -> dict:
+        return lgf_plan_get_stats(self.plan)
 
     def workspace_bytes(self) -> int:
         return lgf_plan_workspace_bytes(self.plan)

@@ -50,12 +50,13 @@ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
 }
 
 // ---- twiddle tables ----
+constexpr int kTwSizes[] = {8, 10, 16, 17, 18, 32, 33, 34, 36};
+// offset of size S in the tables: the sizes above, laid end to end
 __host__ __device__ constexpr int tw_offset(int S) {
-    return S == 8 ? 0 : S == 10 ? 8 : S == 16 ? 18 : S == 18 ? 34 : S == 32 ? 52
-         : S == 33 ? 84 : S == 34 ? 117 : S == 36 ? 151 : -1;
+    return S == 8 ? 0 : S == 10 ? 8 : S == 16 ? 18 : S == 17 ? 34 : S == 18 ? 51 : S == 32 ? 69
+         : S == 33 ? 101 : S == 34 ? 134 : S == 36 ? 168 : -1;
 }
-constexpr int kTwTotal = 187;
-constexpr int kTwSizes[] = {8, 10, 16, 18, 32, 33, 34, 36};
+constexpr int kTwTotal = 204;
 
 // One copy per translation unit (no relocatable device code); each TU fills
 // its own copy through Launch<T>::init_twiddles.

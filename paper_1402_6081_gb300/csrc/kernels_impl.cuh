@@ -441,8 +441,9 @@ cudaError_t Launch<T>::r2c(int S, int n_in, const T* src, int64_t stride, const 
 #define LGF_R2C(SS, NN) \
     if (S == SS && n_in == NN) return launch_r2c<T, SS, NN>(src, stride, items, n, spec, st);
     LGF_R2C(8, 4) LGF_R2C(10, 4) LGF_R2C(10, 5)
-    LGF_R2C(16, 8) LGF_R2C(18, 8) LGF_R2C(18, 9)
-    LGF_R2C(32, 16) LGF_R2C(36, 16) LGF_R2C(36, 17)
+    LGF_R2C(16, 8) LGF_R2C(17, 8) LGF_R2C(17, 9) LGF_R2C(18, 8) LGF_R2C(18, 9)
+    LGF_R2C(32, 16) LGF_R2C(33, 16) LGF_R2C(33, 17) LGF_R2C(34, 16) LGF_R2C(34, 17)
+    LGF_R2C(36, 16) LGF_R2C(36, 17)
 #undef LGF_R2C
     return cudaErrorInvalidValue;
 }
@@ -453,8 +454,8 @@ cudaError_t Launch<T>::c2r(int S, int n_out, const void* spec, const C2RItem* it
 #define LGF_C2R(SS, NN) \
     if (S == SS && n_out == NN) return launch_c2r<T, SS, NN>(spec, items, n, dst, ds, add, add_n, as, st);
     LGF_C2R(8, 4) LGF_C2R(10, 5)
-    LGF_C2R(16, 8) LGF_C2R(18, 9)
-    LGF_C2R(32, 16) LGF_C2R(36, 17)
+    LGF_C2R(16, 8) LGF_C2R(17, 9) LGF_C2R(18, 9)
+    LGF_C2R(32, 16) LGF_C2R(33, 17) LGF_C2R(34, 17) LGF_C2R(36, 17)
 #undef LGF_C2R
     return cudaErrorInvalidValue;
 }

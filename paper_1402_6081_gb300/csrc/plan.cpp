@@ -39,9 +39,15 @@ static lgf_status cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-// FFT length along each axis for the interval levels: the smallest supported
-// length >= 2 n_I - 1 that factors into small radices.
+// FFT length along each axis for the interval levels (any S >= 2 n_I - 1 gives
+// the same linear convolution; these are the lengths the kernels are built for).
 int s_interval(int n_b) { return n_b == 4 ? 10 : n_b == 8 ? 18 : 36; }
+static bool s_interval_supported(int n_b, int S) {
+    if (n_b == 4) return S == 10;
+    if (n_b == 8) return S == 17 || S == 18;
+    if (n_b == 16) return S == 33 || S == 34 || S == 36;
+    return false;
+}
 
 // ---------------------------------------------------------------------------
 // Interpolation stencil (Sec. 2.5): child c node i sits at parent coordinate
@@ -270,6 +276,7 @@ struct lgf_plan_s {
     int64_t n_blocks = 0, n_points = 0;
     int S0 = 0, SI = 0, Lmac = 0;
     std::vector<lgf::DevLevel> lev;
+    std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
     void* W = nullptr;
     lgf::C2RItem* out_items = nullptr;
     int n_out = 0;
@@ -399,23 +406,33 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
                             std::to_string(need));
         }
     }
-    // interaction lists: does level l (1 <= l < L) have any?
+    // interaction lists: sizes per level (level 0: near pairs); Lmac is the
+    // highest level whose interaction list is not empty
     int Lmac = 0;
+    P->pairs.assign(size_t(L) + 1, 0);
+    P->intervals.assign(size_t(L) + 1, 0);
+    P->groups.assign(size_t(L) + 1, 0);
+    for (int l = 0; l <= L; ++l) P->intervals[size_t(l)] = int64_t(lv[size_t(l)].iv.size());
+    for (const I3& a : lv[0].iv)
+        for (int e = 0; e < 27; ++e) {
+            const I3 q{a[0] + e % 3 - 1, a[1] + (e / 3) % 3 - 1, a[2] + e / 9 - 1};
+            P->pairs[0] += lv[0].iv_index.count(pack(q));
+        }
     for (int l = 1; l < L; ++l) {
         const auto& L_ = lv[size_t(l)];
-        bool any = false;
+        int64_t n = 0;
         for (const I3& a : L_.iv) {
             const I3 pp = parent_of(a);
-            for (int e = 0; e < 216 && !any; ++e) {
+            for (int e = 0; e < 216; ++e) {
                 const int cx = e & 1, cy = (e >> 1) & 1, cz = (e >> 2) & 1, ee = e >> 3;
                 const I3 q{2 * (pp[0] + ee % 3 - 1) + cx, 2 * (pp[1] + (ee / 3) % 3 - 1) + cy,
                            2 * (pp[2] + ee / 9 - 1) + cz};
-                if (!near(a, q) && L_.iv_index.count(pack(q))) any = true;
+                if (!near(a, q) && L_.iv_index.count(pack(q))) ++n;
             }
-            if (any) break;
         }
-        lv[size_t(l)].m2l = any;
-        if (any) Lmac = l;
+        P->pairs[size_t(l)] = n;
+        lv[size_t(l)].m2l = n > 0;
+        if (n > 0) Lmac = l;
     }
     P->Lmac = Lmac;
     // sibling groups and slots for levels 0..Lmac
@@ -432,6 +449,7 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         std::sort(L_.groups.begin(), L_.groups.end(),
                   [&](const I3& a, const I3& b) { return morton(a, lo) < morton(b, lo); });
         for (size_t i = 0; i < L_.groups.size(); ++i) L_.group_index[pack(L_.groups[i])] = int(i);
+        P->groups[size_t(l)] = int64_t(L_.groups.size());
     }
     // ---- device objects ----
     const size_t elem = P->prec == LGF_FP64 ? sizeof(double) : sizeof(float);
@@ -655,6 +673,13 @@ lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double* W) {
 
 lgf_status lgf_plan_create(const int32_t* block_ijk, int64_t n_blocks, int32_t n_b, int32_t n_levels,
                            int32_t interp_order, int32_t precision, int32_t interp_mode, lgf_plan* out) {
+    return lgf_plan_create_ex(block_ijk, n_blocks, n_b, n_levels, interp_order, precision, interp_mode,
+                              nullptr, out);
+}
+
+lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_t n_b, int32_t n_levels,
+                              int32_t interp_order, int32_t precision, int32_t interp_mode,
+                              const lgf_plan_options* opts, lgf_plan* out) {
     if (!out) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: out is NULL");
     *out = nullptr;
     if (!block_ijk || n_blocks < 1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need n_blocks >= 1 block indices");
@@ -680,6 +705,13 @@ lgf_status lgf_plan_create(const int32_t* block_ijk, int64_t n_blocks, int32_t n
     P->n_points = n_blocks * int64_t(n_b) * n_b * n_b;
     P->S0 = s_level0(n_b);
     P->SI = s_interval(n_b);
+    if (opts && opts->fft_size_interval != 0) {
+        if (!s_interval_supported(n_b, opts->fft_size_interval))
+            return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: fft_size_interval " +
+                                                 std::to_string(opts->fft_size_interval) +
+                                                 " is not built for n_b = " + std::to_string(n_b));
+        P->SI = opts->fft_size_interval;
+    }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
     s = build_plan(P.get(), block_ijk);
@@ -694,6 +726,27 @@ lgf_status lgf_plan_workspace_bytes(lgf_plan plan, size_t* bytes) {
     for (auto& D : plan->lev)
         if (D.kh) b += D.kh->bytes;
     *bytes = b;
+    return ok();
+}
+
+lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
+    if (!plan || !st) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_get_stats: NULL argument");
+    std::memset(st, 0, sizeof(*st));
+    st->n_points = plan->n_points;
+    st->n_blocks = plan->n_blocks;
+    st->n_levels = plan->L;
+    st->top_product_level = plan->Lmac;
+    st->fft_size_level0 = plan->S0;
+    st->fft_size_interval = plan->SI;
+    for (int l = 0; l <= plan->L && l <= LGF_MAX_LEVELS; ++l) {
+        st->pairs[l] = plan->pairs[size_t(l)];
+        st->intervals[l] = plan->intervals[size_t(l)];
+        st->groups[l] = plan->groups[size_t(l)];
+        if (l <= plan->Lmac && plan->lev[size_t(l)].m2l) st->nw[l] = nw_of(l == 0 ? plan->S0 : plan->SI);
+    }
+    size_t b = 0;
+    lgf_plan_workspace_bytes(plan, &b);
+    st->workspace_bytes = int64_t(b);
     return ok();
 }
 
