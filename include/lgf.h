@@ -174,6 +174,36 @@ lgf_status lgf_plan_set_timing(lgf_plan plan, int32_t capacity);
 lgf_status lgf_plan_timings(lgf_plan plan, int32_t max_kernels, int32_t *n_kernels, char *names,
                             double *total_ms, int32_t *count, int32_t *launches_per_solve);
 
+/*
+ * lgf_solve_blocks_noalloc - solves every block as its own isolated problem,
+ * u_b = G * f_b over block b alone (each block is a separate one-block domain,
+ * as lgf_solve computes for a one-block plan), without allocating any device
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc while they run (allocator hooks, loops whose memory was
+ * fixed up front, frameworks that own the device heap).
+ *
+ * All working memory (block spectra, kernel spectra, item tables) lives in one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits.  The first call on a device, with that device
+ * current, looks up the array's device address and uploads the tables with
+ * synchronous copies; make that first call before any stream capture.  Each
+ * (n_b, precision) pair's first call also uploads its kernel spectrum.
+ *
+ *   f_dev, u_dev  device pointers, n_blocks * n_b^3 values of the precision,
+ *                 block-major with x fastest (as lgf_solve); must not overlap
+ *   n_blocks      1 .. lgf_noalloc_max_blocks(n_b, precision); more is
+ *                 LGF_ERR_INVALID_ARG (232 for n_b = 16 in FP32, 116 in FP64)
+ *   n_b           4, 8 or 16;  precision  LGF_FP32 or LGF_FP64
+ *   stream        cudaStream_t; asynchronous after the first call
+ *
+ * Every call shares the array and it keeps the last call's contents; each
+ * call writes all it reads.  Calls that overlap on the GPU (other streams or
+ * host threads) race on the array and must be serialised by the caller.
+ */
+lgf_status lgf_solve_blocks_noalloc(const void *f_dev, void *u_dev, int64_t n_blocks, int32_t n_b,
+                                    int32_t precision, void *stream);
+lgf_status lgf_noalloc_max_blocks(int32_t n_b, int32_t precision, int64_t *max_blocks);
+
 /* Frees the plan and its workspace (waits for its device work first). */
 lgf_status lgf_destroy(lgf_plan plan);
 

@@ -44,6 +44,9 @@ _SIGS = {
     "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "lgf_solve_blocks_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "lgf_noalloc_max_blocks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_green_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lgf_interp_weights": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
@@ -209,6 +212,18 @@ def lgf_plan_timings(plan: int):
         nm = names.raw[32 * j: 32 * (j + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (tot[j], cnt[j])
     return out, per.value
+
+
+def lgf_solve_blocks_noalloc(f, u, n_blocks: int, n_b: int, precision: int, stream=None) -> None:
+    """Isolated one-block solves with no device allocation (see include/lgf.h)."""
+    _check(library().lgf_solve_blocks_noalloc(_dev_ptr(f), _dev_ptr(u), n_blocks, n_b, precision,
+                                              _stream_ptr(stream)), "lgf_solve_blocks_noalloc")
+
+
+def lgf_noalloc_max_blocks(n_b: int, precision: int) -> int:
+    v = ctypes.c_int64()
+    _check(library().lgf_noalloc_max_blocks(n_b, precision, ctypes.byref(v)), "lgf_noalloc_max_blocks")
+    return v.value
 
 
 def lgf_destroy(plan: int) -> None:

@@ -30,6 +30,13 @@ void fft_inplace(std::complex<double>* x, int n, int stride, int sign);
 void fft_lines(std::complex<double>* base, int n, int stride, int count, int64_t line_stride,
                int sign);
 
+// ---- kernel spectra (plan.cpp) ----
+// Spectrum (NW values, w = (kz*S + ky)*NX + kx, scaled by 1/S^3) of the kernel
+// vector k(m) = G(h (m - d n_b)), |m_a| <= n - 1, placed at m mod S; tab is the
+// dense |offset| table G(h*(a,b,c)) of edge V + 1.
+void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
+                     std::complex<double>* outw);
+
 // ---- interpolation stencils (plan.cpp) ----
 // W[c][i][p] (2 x n_I x n_I) for child c node i and parent node p.
 std::vector<double> interp_weights(int n_b, int n_max);

@@ -117,8 +117,8 @@ struct SpecKey {
     }
 };
 
-static void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
-                            std::complex<double>* outw /* NW */) {
+void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
+                     std::complex<double>* outw /* NW */) {
     const int NX = nx_of(S);
     std::vector<std::complex<double>> C(size_t(S) * S * NX);
     std::vector<double> k(size_t(S) * S * S, 0.0);
