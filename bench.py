@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fft-size", type=int, default=0,
+                    help="FFT length per axis at the interval levels (0 = library default)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -224,7 +226,7 @@ def main():
 
     def make(prec):
         dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
-        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec)
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=args.fft_size)
         f = torch.from_numpy(p.f).to(dt).cuda()
         u = torch.empty_like(f)
         return s, f, u
@@ -302,9 +304,11 @@ def main():
     dom_name, (dom_tot, dom_cnt) = dom
     dom_ms = dom_tot / dom_cnt
     pk, src = peaks()
-    pairs = interaction_pairs(p.blocks, p.n_levels)
-    S0, SI = 2 * p.n_b, 36
-    nw = {0: (S0 // 2 + 1) * S0 * S0, 1: (SI // 2 + 1) * SI * SI}
+    st = s32.stats()
+    pairs = {l: st["pairs"][l] for l in range(p.n_levels)}
+    assert pairs == interaction_pairs(p.blocks, p.n_levels)
+    S0, SI = st["fft_size_level0"], st["fft_size_interval"]
+    nw = {0: st["nw"][0], 1: st["nw"][1]}
     roof = None
     if dom_name.startswith("mac_"):
         lvl = 0 if dom_name == "mac_level0" else 1

@@ -234,11 +234,11 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
 // The CTA stages the coefficients of its 32 frequencies in shared memory
 // (343 x 32), shared by its G groups.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mac_interval(const cx<T>* __restrict__ fh,
-                                                      const cx<T>* __restrict__ kh,
-                                                      cx<T>* __restrict__ uh,
-                                                      const int* __restrict__ gnbr, int n_groups,
-                                                      int64_t NW) {
+__global__ void __launch_bounds__(256, 2) k_mac_interval(const cx<T>* __restrict__ fh,
+                                                         const cx<T>* __restrict__ kh,
+                                                         cx<T>* __restrict__ uh,
+                                                         const int* __restrict__ gnbr, int n_groups,
+                                                         int64_t NW) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
@@ -254,19 +254,42 @@ __global__ void __launch_bounds__(256) k_mac_interval(const cx<T>* __restrict__ 
     if (g >= n_groups) return;
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
+    // neighbour groups present (bit e), the group itself excluded
+    const int* nb = gnbr + int64_t(g) * 27;
+    unsigned mask = 0;
+#pragma unroll
+    for (int e = 0; e < 27; ++e)
+        if (e != 13 && __ldg(nb + e) >= 0) mask |= 1u << e;
     cx<T> acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
-    const int* nb = gnbr + int64_t(g) * 27;
-#pragma unroll 1
-    for (int e = 0; e < 27; ++e) {
-        if (e == 13) continue;
-        const int q = __ldg(nb + e);
-        if (q < 0) continue;
-        const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = e / 9 - 1;
-        cx<T> F[8];
+    if (mask == 0) {
+        if (w < NW) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) F[c] = ldg_cx(fh + (int64_t(q) * 8 + c) * NW + wc);
+            for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NW + w] = acc[c];
+        }
+        return;
+    }
+    // software pipeline: the 8 source spectra of the next neighbour group are
+    // loaded before the products of the current one
+    int e = __ffs(mask) - 1;
+    mask &= mask - 1;
+    cx<T> F[8];
+    {
+        const cx<T>* src = fh + int64_t(__ldg(nb + e)) * 8 * NW + wc;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + int64_t(c) * NW);
+    }
+    while (true) {
+        const int en = mask ? __ffs(mask) - 1 : -1;
+        mask &= mask - 1;
+        cx<T> Fn[8];
+        if (en >= 0) {
+            const cx<T>* src = fh + int64_t(__ldg(nb + en)) * 8 * NW + wc;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) Fn[c] = ldg_cx(src + int64_t(c) * NW);
+        }
+        const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = e / 9 - 1;
         const cx<T>* kb = sk + ((2 * ex + 3) + 7 * (2 * ey + 3) + 49 * (2 * ez + 3)) * 32 + threadIdx.x;
         cx<T> kk[27];
 #pragma unroll
@@ -284,6 +307,10 @@ __global__ void __launch_bounds__(256) k_mac_interval(const cx<T>* __restrict__ 
                           dz = (cs >> 2) - (ct >> 2);
                 acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
             }
+        if (en < 0) break;
+        e = en;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) F[c] = Fn[c];
     }
     if (w < NW) {
 #pragma unroll
@@ -292,114 +319,173 @@ __global__ void __launch_bounds__(256) k_mac_interval(const cx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Reg (Eq. alg_reg): parent sources = sum over the 8 children c of
-// (W_cz^T x W_cy^T x W_cx^T) child sources.  One CTA per parent interval;
-// W[c][i][p] is the weight of parent node p for child node i.  A level-1 child
-// is a block: its sources occupy nodes [0, n_b)^3 and its last node plane is 0.
-template <typename T>
-__global__ void k_reg(int n_b, const T* __restrict__ child_src, int child_is_block,
-                      const int* __restrict__ child_index, const int* __restrict__ parent_slot,
-                      T* __restrict__ dst, const T* __restrict__ W) {
-    const int nI = n_b + 1, N3 = nI * nI * nI;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Ws = reinterpret_cast<T*>(smem_raw);   // [2][nI][nI]
-    T* in = Ws + 2 * nI * nI;
-    T* t1 = in + N3;
-    T* acc = t1 + N3;
-    for (int i = threadIdx.x; i < 2 * nI * nI; i += blockDim.x) Ws[i] = W[i];
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) acc[i] = T(0);
-    for (int c = 0; c < 8; ++c) {
-        const int src = child_index[blockIdx.x * 8 + c];
-        if (src < 0) continue;
-        const int cxp = c & 1, cyp = (c >> 1) & 1, czp = c >> 2;
-        __syncthreads();
-        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-            const int x = i % nI, y = (i / nI) % nI, z = i / (nI * nI);
-            T v;
-            if (child_is_block)
-                v = (x < n_b && y < n_b && z < n_b)
-                        ? child_src[int64_t(src) * n_b * n_b * n_b + (z * n_b + y) * n_b + x]
-                        : T(0);
-            else
-                v = child_src[int64_t(src) * N3 + i];
-            in[i] = v;
-        }
-        __syncthreads();
-        const T* Wx = Ws + cxp * nI * nI;
-        const T* Wy = Ws + cyp * nI * nI;
-        const T* Wz = Ws + czp * nI * nI;
-        // x: t1[z][y][p] = sum_i Wx[i][p] in[z][y][i]
-        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-            const int p = i % nI, zy = i / nI;
-            T s = T(0);
-            for (int k = 0; k < nI; ++k) s = fma(Wx[k * nI + p], in[zy * nI + k], s);
-            t1[i] = s;
-        }
-        __syncthreads();
-        // y: in[z][q][p] = sum_j Wy[j][q] t1[z][j][p]
-        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-            const int p = i % nI, q = (i / nI) % nI, z = i / (nI * nI);
-            T s = T(0);
-            for (int k = 0; k < nI; ++k) s = fma(Wy[k * nI + q], t1[(z * nI + k) * nI + p], s);
-            in[i] = s;
-        }
-        __syncthreads();
-        // z: acc[r][q][p] += sum_k Wz[k][r] in[k][q][p]
-        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-            const int qp = i % (nI * nI), r = i / (nI * nI);
-            T s = acc[i];
-            for (int k = 0; k < nI; ++k) s = fma(Wz[k * nI + r], in[k * nI * nI + qp], s);
-            acc[i] = s;
-        }
+// Reg (Eq. alg_reg) and Interp (Eq. alg_interp): tensor products of the 1D
+// matrices W[c][i][p] (weight of parent node p for child node i).  The two
+// n_I x n_I matrices travel as a by-value kernel parameter, so with every loop
+// unrolled each weight is a constant-bank operand of an FMA.  One thread holds
+// one line of n_I values in registers and produces the n_I outputs of that
+// line; the three axes are three such passes through shared memory.
+template <typename T, int NI>
+struct InterpW {
+    T w[2][NI][NI];
+};
+
+// out[p] = sum_i W[c][i][p] in[i]   (adjoint: child line -> parent line).
+// c is uniform over the CTA; each branch is a fully unrolled dense product.
+template <typename T, int NI>
+__device__ __forceinline__ void apply_wt(const InterpW<T, NI>& W, int c, const T (&in)[NI], T (&out)[NI]) {
+#pragma unroll
+    for (int p = 0; p < NI; ++p) out[p] = T(0);
+    if (c == 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) out[p] = fma(W.w[0][i][p], in[i], out[p]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) out[p] = fma(W.w[1][i][p], in[i], out[p]);
     }
-    __syncthreads();
-    T* out = dst + int64_t(parent_slot[blockIdx.x]) * N3;
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) out[i] = acc[i];
 }
 
-// ---------------------------------------------------------------------------
-// Interp (Eq. alg_interp): u[slot] += (W_cz x W_cy x W_cx) up[parent] with
-// c = slot & 7 the interval's position among its siblings.
-template <typename T>
-__global__ void k_interp(int n_b, const int* __restrict__ slot, const int* __restrict__ parent,
-                         T* __restrict__ u, const T* __restrict__ up, const T* __restrict__ W) {
-    const int nI = n_b + 1, N3 = nI * nI * nI;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Ws = reinterpret_cast<T*>(smem_raw);
-    T* a = Ws + 2 * nI * nI;
-    T* b = a + N3;
+// out[i] = sum_p W[c][i][p] in[p]   (interpolation: parent line -> child line)
+template <typename T, int NI>
+__device__ __forceinline__ void apply_w(const InterpW<T, NI>& W, int c, const T (&in)[NI], T (&out)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) out[i] = T(0);
+    if (c == 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) out[i] = fma(W.w[0][i][p], in[p], out[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) out[i] = fma(W.w[1][i][p], in[p], out[i]);
+    }
+}
+
+constexpr int kLineThreads = 320;   // >= 17*17 lines of a pass
+
+// Reg: one CTA per parent interval; the parent's sources accumulate in the
+// registers of the z-pass threads across the 8 children.  A level-1 child is a
+// block: its sources occupy nodes [0, n_b)^3 and its last node plane is 0.
+// One shared buffer: every pass reads its whole line into registers, then a
+// barrier, then writes.
+template <typename T, int NI>
+__global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ child_src, int child_is_block,
+                                                      const int* __restrict__ child_index,
+                                                      const int* __restrict__ parent_slot,
+                                                      T* __restrict__ dst, const InterpW<T, NI> W) {
+    constexpr int NB = NI - 1, N2 = NI * NI, N3 = NI * NI * NI;
+    __shared__ T a[N3];
+    const int t = threadIdx.x;
+    const bool act = t < N2;
+    T acc[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) acc[r] = T(0);
+    for (int c = 0; c < 8; ++c) {
+        const int src = child_index[blockIdx.x * 8 + c];
+        if (src < 0) continue;                               // uniform over the CTA
+        const int cxp = c & 1, cyp = (c >> 1) & 1, czp = c >> 2;
+        T in[NI], out[NI];
+        // x pass: line (z, y) of the child -> a[z][y][p]
+        if (act) {
+            const int y = t % NI, z = t / NI;
+            if (child_is_block) {
+                const T* row = child_src + int64_t(src) * NB * NB * NB + (z * NB + y) * NB;
+                const bool live = y < NB && z < NB;
+#pragma unroll
+                for (int x = 0; x < NI; ++x) in[x] = (live && x < NB) ? row[x] : T(0);
+            } else {
+                const T* row = child_src + int64_t(src) * N3 + (z * NI + y) * NI;
+#pragma unroll
+                for (int x = 0; x < NI; ++x) in[x] = row[x];
+            }
+            apply_wt(W, cxp, in, out);
+        }
+        __syncthreads();                                      // previous child's z pass is done with a
+        if (act) {
+#pragma unroll
+            for (int p = 0; p < NI; ++p) a[t * NI + p] = out[p];
+        }
+        __syncthreads();
+        // y pass: line (z, p) -> a[z][q][p]
+        if (act) {
+            const int p = t % NI, z = t / NI;
+#pragma unroll
+            for (int y = 0; y < NI; ++y) in[y] = a[(z * NI + y) * NI + p];
+            apply_wt(W, cyp, in, out);
+        }
+        __syncthreads();
+        if (act) {
+            const int p = t % NI, z = t / NI;
+#pragma unroll
+            for (int q = 0; q < NI; ++q) a[(z * NI + q) * NI + p] = out[q];
+        }
+        __syncthreads();
+        // z pass: line (q, p) -> acc[r]
+        if (act) {
+#pragma unroll
+            for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
+            apply_wt(W, czp, in, out);
+#pragma unroll
+            for (int r = 0; r < NI; ++r) acc[r] += out[r];
+        }
+    }
+    if (act) {
+        T* o = dst + int64_t(parent_slot[blockIdx.x]) * N3 + t;
+#pragma unroll
+        for (int r = 0; r < NI; ++r) o[r * N2] = acc[r];
+    }
+}
+
+// Interp: u[slot] += (W_cz x W_cy x W_cx) up[parent], c = slot & 7.
+template <typename T, int NI>
+__global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__ slot,
+                                                         const int* __restrict__ parent, T* __restrict__ u,
+                                                         const T* __restrict__ up, const InterpW<T, NI> W) {
+    constexpr int N2 = NI * NI, N3 = NI * NI * NI;
+    __shared__ T a[N3];
+    const int t = threadIdx.x;
+    const bool act = t < N2;
     const int s = slot[blockIdx.x];
     const int c = s & 7, cxp = c & 1, cyp = (c >> 1) & 1, czp = c >> 2;
-    for (int i = threadIdx.x; i < 2 * nI * nI; i += blockDim.x) Ws[i] = W[i];
     const T* U = up + int64_t(parent[blockIdx.x]) * N3;
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) a[i] = U[i];
-    __syncthreads();
-    const T* Wx = Ws + cxp * nI * nI;
-    const T* Wy = Ws + cyp * nI * nI;
-    const T* Wz = Ws + czp * nI * nI;
-    // x: b[pz][py][ix] = sum_px Wx[ix][px] a[pz][py][px]
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-        const int ix = i % nI, zy = i / nI;
-        T acc = T(0);
-        for (int k = 0; k < nI; ++k) acc = fma(Wx[ix * nI + k], a[zy * nI + k], acc);
-        b[i] = acc;
+    T in[NI], out[NI];
+    // x pass: line (pz, py) -> a[pz][py][ix]
+    if (act) {
+#pragma unroll
+        for (int x = 0; x < NI; ++x) in[x] = U[t * NI + x];
+        apply_w(W, cxp, in, out);
+#pragma unroll
+        for (int x = 0; x < NI; ++x) a[t * NI + x] = out[x];
     }
     __syncthreads();
-    // y: a[pz][iy][ix] = sum_py Wy[iy][py] b[pz][py][ix]
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-        const int ix = i % nI, iy = (i / nI) % nI, z = i / (nI * nI);
-        T acc = T(0);
-        for (int k = 0; k < nI; ++k) acc = fma(Wy[iy * nI + k], b[(z * nI + k) * nI + ix], acc);
-        a[i] = acc;
+    // y pass: line (pz, ix) -> a[pz][iy][ix]
+    if (act) {
+        const int ix = t % NI, z = t / NI;
+#pragma unroll
+        for (int y = 0; y < NI; ++y) in[y] = a[(z * NI + y) * NI + ix];
+        apply_w(W, cyp, in, out);
     }
     __syncthreads();
-    // z: u[iz][iy][ix] += sum_pz Wz[iz][pz] a[pz][iy][ix]
-    T* out = u + int64_t(s) * N3;
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-        const int yx = i % (nI * nI), iz = i / (nI * nI);
-        T acc = T(0);
-        for (int k = 0; k < nI; ++k) acc = fma(Wz[iz * nI + k], a[k * nI * nI + yx], acc);
-        out[i] += acc;
+    if (act) {
+        const int ix = t % NI, z = t / NI;
+#pragma unroll
+        for (int y = 0; y < NI; ++y) a[(z * NI + y) * NI + ix] = out[y];
+    }
+    __syncthreads();
+    // z pass: line (iy, ix) -> u[iz][iy][ix] +=
+    if (act) {
+#pragma unroll
+        for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
+        apply_w(W, czp, in, out);
+        T* o = u + int64_t(s) * N3 + t;
+#pragma unroll
+        for (int z = 0; z < NI; ++z) o[z * N2] += out[z];
     }
 }
 
@@ -490,31 +576,44 @@ cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, co
     return cudaGetLastError();
 }
 
+template <typename T, int NI>
+static dev::InterpW<T, NI> pack_w(const T* W) {
+    dev::InterpW<T, NI> p;
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < NI; ++i)
+            for (int q = 0; q < NI; ++q) p.w[c][i][q] = W[(c * NI + i) * NI + q];
+    return p;
+}
+
+// W here is the host copy of the 2 x n_I x n_I matrices (plan precision).
 template <typename T>
 cudaError_t Launch<T>::reg(int n_b, int /*n_max*/, const T* child_src, int child_is_block,
                            const int* child_index, const int* parent_slot, int n_parents, T* dst,
                            const T* W, cudaStream_t st) {
     if (n_parents == 0) return cudaSuccess;
-    const int nI = n_b + 1;
-    const size_t smem = sizeof(T) * (2 * nI * nI + 3 * nI * nI * nI);
-    auto k = dev::k_reg<T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    k<<<n_parents, 256, smem, st>>>(n_b, child_src, child_is_block, child_index, parent_slot, dst, W);
-    return cudaGetLastError();
+#define LGF_REG(NI)                                                                                   \
+    if (n_b + 1 == NI) {                                                                              \
+        dev::k_reg<T, NI><<<n_parents, dev::kLineThreads, 0, st>>>(child_src, child_is_block, child_index, \
+                                                                  parent_slot, dst, pack_w<T, NI>(W));  \
+        return cudaGetLastError();                                                                    \
+    }
+    LGF_REG(5) LGF_REG(9) LGF_REG(17)
+#undef LGF_REG
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t Launch<T>::interp(int n_b, const int* slot, const int* parent, int n_items, T* u,
                               const T* up, const T* W, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    const int nI = n_b + 1;
-    const size_t smem = sizeof(T) * (2 * nI * nI + 2 * nI * nI * nI);
-    auto k = dev::k_interp<T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    k<<<n_items, 256, smem, st>>>(n_b, slot, parent, u, up, W);
-    return cudaGetLastError();
+#define LGF_INTERP(NI)                                                                                   \
+    if (n_b + 1 == NI) {                                                                                 \
+        dev::k_interp<T, NI><<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W)); \
+        return cudaGetLastError();                                                                       \
+    }
+    LGF_INTERP(5) LGF_INTERP(9) LGF_INTERP(17)
+#undef LGF_INTERP
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lgf

@@ -277,7 +277,9 @@ struct lgf_plan_s {
     int S0 = 0, SI = 0, Lmac = 0;
     std::vector<lgf::DevLevel> lev;
     std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
-    void* W = nullptr;
+    void* W = nullptr;                  // device copy (unused by the kernels, kept for tools)
+    std::vector<float> Wf;              // host copies passed by value to Reg / Interp
+    std::vector<double> Wd;
     lgf::C2RItem* out_items = nullptr;
     int n_out = 0;
     std::vector<void*> allocs;
@@ -543,6 +545,8 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
     // interpolation weights in the plan precision
     {
         std::vector<double> W = interp_weights(nb, P->n_max);
+        P->Wd = W;
+        P->Wf.assign(W.begin(), W.end());
         lgf_status s;
         if (P->prec == LGF_FP64) {
             double* d = nullptr;
@@ -581,7 +585,9 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     const int nb = P->n_b, nI = P->n_I;
     const int64_t n3 = int64_t(nI) * nI * nI, b3 = int64_t(nb) * nb * nb;
     auto& lev = P->lev;
-    const T* W = static_cast<const T*>(P->W);
+    const T* W = nullptr;
+    if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(P->Wd.data());
+    else W = reinterpret_cast<const T*>(P->Wf.data());
     cudaError_t e;
     // Step 1: upward pass
     e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
