@@ -233,88 +233,134 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
 // with zeros at the 27 near ones (|d| <= 1), which removes the list test.
 // The CTA stages the coefficients of its 32 frequencies in shared memory
 // (343 x 32), shared by its G groups.
+constexpr int kMacWarps = 12;
+
+// One warp's walk over the (group, neighbour) pairs it owns: groups
+// g0 + warp, g0 + warp + kMacWarps, ... below g1, and for each group the
+// present neighbour groups e != 13 in increasing order.
+struct MacWalk {
+    int g, e;            // current pair (e < 0: group without neighbours)
+    unsigned mask;       // neighbours of g not yet visited
+};
+
+__device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g) {
+    const int* nb = gnbr + int64_t(g) * 27;
+    unsigned m = 0;
+#pragma unroll
+    for (int e = 0; e < 27; ++e)
+        if (e != 13 && __ldg(nb + e) >= 0) m |= 1u << e;
+    return m;
+}
+
+// advance to the next pair; returns false past the warp's last group
+__device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gnbr, int g1) {
+    if (it.mask) {
+        it.e = __ffs(it.mask) - 1;
+        it.mask &= it.mask - 1;
+        return true;
+    }
+    it.g += kMacWarps;
+    if (it.g >= g1) return false;
+    it.mask = nbr_mask(gnbr, it.g);
+    if (it.mask) {
+        it.e = __ffs(it.mask) - 1;
+        it.mask &= it.mask - 1;
+    } else {
+        it.e = -1;
+    }
+    return true;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void mac_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh,
+                                         const int* __restrict__ gnbr, const MacWalk& it, int64_t wc) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    if (it.e < 0) return;
+    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NW) + wc;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NW);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_mac_interval(const cx<T>* __restrict__ fh,
-                                                         const cx<T>* __restrict__ kh,
-                                                         cx<T>* __restrict__ uh,
-                                                         const int* __restrict__ gnbr, int n_groups,
-                                                         int64_t NW) {
+__device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], const cx<T>* __restrict__ sk,
+                                          int e) {
+    // centre offset d = 2e of this neighbour in the 7^3 coefficient rows
+    const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;      // 0..2
+    const cx<T>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 32 + threadIdx.x;
+    cx<T> kk[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
+#pragma unroll
+    for (int ct = 0; ct < 8; ++ct)
+#pragma unroll
+        for (int cs = 0; cs < 8; ++cs) {
+            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
+            acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
+        }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_interval(const cx<T>* __restrict__ fh,
+                                                                   const cx<T>* __restrict__ kh,
+                                                                   cx<T>* __restrict__ uh,
+                                                                   const int* __restrict__ gnbr, int n_groups,
+                                                                   int groups_per_cta) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
-    for (int i = tid; i < 343 * 32; i += nthr) {
+    for (int i = tid; i < 343 * 32; i += 32 * kMacWarps) {
         const int d = i >> 5, lane = i & 31;
         const int64_t w = w0 + lane;
         sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NW + w) : czero<T>();
     }
     __syncthreads();
-    const int g = blockIdx.x * blockDim.y + threadIdx.y;
-    if (g >= n_groups) return;
+    const int g0 = blockIdx.x * groups_per_cta;
+    const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
-    // neighbour groups present (bit e), the group itself excluded
-    const int* nb = gnbr + int64_t(g) * 27;
-    unsigned mask = 0;
-#pragma unroll
-    for (int e = 0; e < 27; ++e)
-        if (e != 13 && __ldg(nb + e) >= 0) mask |= 1u << e;
-    cx<T> acc[8];
+    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0u};
+    if (!mac_next(cur, gnbr, g1)) return;
+    cx<T> Fa[8], Fb[8], acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
-    if (mask == 0) {
-        if (w < NW) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NW + w] = acc[c];
-        }
-        return;
-    }
-    // software pipeline: the 8 source spectra of the next neighbour group are
-    // loaded before the products of the current one
-    int e = __ffs(mask) - 1;
-    mask &= mask - 1;
-    cx<T> F[8];
-    {
-        const cx<T>* src = fh + int64_t(__ldg(nb + e)) * 8 * NW + wc;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + int64_t(c) * NW);
-    }
+    mac_load<T, S>(Fa, fh, gnbr, cur, wc);
+    // two pairs per trip so the prefetch buffers alternate without copies
     while (true) {
-        const int en = mask ? __ffs(mask) - 1 : -1;
-        mask &= mask - 1;
-        cx<T> Fn[8];
-        if (en >= 0) {
-            const cx<T>* src = fh + int64_t(__ldg(nb + en)) * 8 * NW + wc;
+        MacWalk nxt = cur;
+        bool more = mac_next(nxt, gnbr, g1);
+        if (more) mac_load<T, S>(Fb, fh, gnbr, nxt, wc);
+        if (cur.e >= 0) mac_block(acc, Fa, sk, cur.e);
+        if (!more || nxt.g != cur.g) {
+            if (w < NW) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) Fn[c] = ldg_cx(src + int64_t(c) * NW);
-        }
-        const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = e / 9 - 1;
-        const cx<T>* kb = sk + ((2 * ex + 3) + 7 * (2 * ey + 3) + 49 * (2 * ez + 3)) * 32 + threadIdx.x;
-        cx<T> kk[27];
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx)
-                    kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
-#pragma unroll
-        for (int ct = 0; ct < 8; ++ct)
-#pragma unroll
-            for (int cs = 0; cs < 8; ++cs) {
-                const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1),
-                          dz = (cs >> 2) - (ct >> 2);
-                acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NW + w] = acc[c];
             }
-        if (en < 0) break;
-        e = en;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) F[c] = Fn[c];
-    }
-    if (w < NW) {
+            for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
+        }
+        if (!more) break;
+        cur = nxt;
+        nxt = cur;
+        more = mac_next(nxt, gnbr, g1);
+        if (more) mac_load<T, S>(Fa, fh, gnbr, nxt, wc);
+        if (cur.e >= 0) mac_block(acc, Fb, sk, cur.e);
+        if (!more || nxt.g != cur.g) {
+            if (w < NW) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NW + w] = acc[c];
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NW + w] = acc[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
+        }
+        if (!more) break;
+        cur = nxt;
     }
 }
 
@@ -559,21 +605,39 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
-                                    int n_groups, int S, cudaStream_t st) {
+template <typename T, int S>
+static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
+                                       cudaStream_t st) {
     const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
-    auto k = dev::k_mac_interval<T>;
+    auto k = dev::k_mac_interval<T, S>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (n_groups == 0) return cudaSuccess;
-    const int64_t NW = nw_of(S);
-    const int G = 8;
-    dim3 block(32, G), grid((n_groups + G - 1) / G, unsigned((NW + 31) / 32));
-    k<<<grid, block, smem, st>>>(static_cast<const dev::cx<T>*>(fh),
-                                 static_cast<const dev::cx<T>*>(kh),
-                                 static_cast<dev::cx<T>*>(uh), gnbr, n_groups, NW);
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    const int nchunks = int((NW + 31) / 32);
+    // groups per CTA: at least one per warp, and enough CTAs for ~4 waves of
+    // two CTAs per SM; several groups per warp even out uneven neighbour counts
+    int per = dev::kMacWarps;
+    const int per_sm = sizeof(T) == 4 ? 2 : 1;
+    while (per < n_groups && int64_t((n_groups + 2 * per - 1) / (2 * per)) * nchunks >= 4 * per_sm * 152) per *= 2;
+    dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, nchunks);
+    k<<<grid, block, smem, st>>>(static_cast<const dev::cx<T>*>(fh), static_cast<const dev::cx<T>*>(kh),
+                                 static_cast<dev::cx<T>*>(uh), gnbr, n_groups, per);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
+                                    int n_groups, int S, cudaStream_t st) {
+    switch (S) {
+        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, n_groups, st);
+        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, n_groups, st);
+        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, n_groups, st);
+        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, n_groups, st);
+        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, n_groups, st);
+        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, n_groups, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int NI>

@@ -41,7 +41,7 @@ static lgf_status cuda_fail(cudaError_t e, const char* where) {
 
 // FFT length along each axis for the interval levels (any S >= 2 n_I - 1 gives
 // the same linear convolution; these are the lengths the kernels are built for).
-int s_interval(int n_b) { return n_b == 4 ? 10 : n_b == 8 ? 18 : 36; }
+int s_interval(int n_b) { return n_b == 4 ? 10 : n_b == 8 ? 18 : 33; }
 static bool s_interval_supported(int n_b, int S) {
     if (n_b == 4) return S == 10;
     if (n_b == 8) return S == 17 || S == 18;
