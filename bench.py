@@ -190,6 +190,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fft-size", type=int, default=0,
                     help="FFT length per axis at the interval levels (0 = library default)")
+    ap.add_argument("--near-kernel", type=int, default=0, help="level-0 product kernel variant (0 = default)")
+    ap.add_argument("--interval-kernel", type=int, default=0, help="interval product kernel variant (0 = default)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -226,7 +228,8 @@ def main():
 
     def make(prec):
         dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
-        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=args.fft_size)
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=args.fft_size,
+                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel)
         f = torch.from_numpy(p.f).to(dt).cuda()
         u = torch.empty_like(f)
         return s, f, u

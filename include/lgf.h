@@ -93,10 +93,18 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      S_I >= 2 n_I - 1 gives the same linear convolution).
  *                      0 = default.  Supported: n_b = 4: 10; n_b = 8: 17, 18;
  *                      n_b = 16: 33, 34, 36.  The level-0 length is 2 n_b.
+ *   near_kernel        product kernel of level 0: 0 = default, 1 = fully
+ *                      unrolled 4^3-source form, 2 = half-plane pipelined form
+ *   interval_kernel    product kernel of levels >= 1: 0 = default, 1 = one
+ *                      frequency per thread, 2 = two frequencies per thread
+ * All variants compute the same sums (Eq. alg_mult) in the same order per
+ * target; they differ only in scheduling.
  */
 typedef struct {
     int32_t fft_size_interval;
-    int32_t reserved[15];
+    int32_t near_kernel;
+    int32_t interval_kernel;
+    int32_t reserved[13];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */

@@ -47,12 +47,12 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
                                                      const R2CItem* __restrict__ items,
                                                      cx<T>* __restrict__ spec) {
     constexpr int NX = S / 2 + 1;
-    constexpr int64_t NW = int64_t(NX) * S * S;
+    constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
     const R2CItem it = items[blockIdx.x];
     const T* in = src + int64_t(it.src) * src_stride;
-    cx<T>* out = spec + int64_t(it.dst) * NW;
+    cx<T>* out = spec + int64_t(it.dst) * NWS;
 
     // x pass: two real lines per complex transform
     constexpr int NL = NIN * NIN, NP = (NL + 1) / 2;
@@ -113,11 +113,11 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
                                                      const T* __restrict__ add, int add_n,
                                                      int64_t add_stride) {
     constexpr int NX = S / 2 + 1;
-    constexpr int64_t NW = int64_t(NX) * S * S;
+    constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
     const C2RItem it = items[blockIdx.x];
-    const cx<T>* in = spec + int64_t(it.src) * NW;
+    const cx<T>* in = spec + int64_t(it.src) * NWS;
 
     // z pass: lines (kx, ky); keep z < NOUT
     for (int l = threadIdx.x; l < NX * S; l += blockDim.x) {
@@ -188,13 +188,13 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
                                                     const cx<T>* __restrict__ kh,
                                                     cx<T>* __restrict__ uh,
                                                     const int* __restrict__ gnbr, int n_groups,
-                                                    int64_t NW) {
+                                                    int64_t NW, int64_t NWS) {
     const int64_t w = int64_t(blockIdx.y) * 32 + threadIdx.x;
     const int g = blockIdx.x * blockDim.y + threadIdx.y;
     if (g >= n_groups || w >= NW) return;
     cx<T> k[27];
 #pragma unroll
-    for (int d = 0; d < 27; ++d) k[d] = ldg_cx(kh + int64_t(d) * NW + w);
+    for (int d = 0; d < 27; ++d) k[d] = ldg_cx(kh + int64_t(d) * NWS + w);
     cx<T> acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
                 const int q = __ldg(nb + (ex + 1) + 3 * (ey + 1) + 9 * (ez + 1));
                 if (q < 0) continue;
                 const int cs = (tx - 2 * ex) + 2 * (ty - 2 * ey) + 4 * (tz - 2 * ez);
-                const cx<T> F = ldg_cx(fh + (int64_t(q) * 8 + cs) * NW + w);
+                const cx<T> F = ldg_cx(fh + (int64_t(q) * 8 + cs) * NWS + w);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int dx = tx - (c & 1), dy = ty - ((c >> 1) & 1), dz = tz - (c >> 2);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
                 }
             }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NW + w] = acc[c];
+    for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NWS + w] = acc[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -274,11 +274,11 @@ __device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gn
 template <typename T, int S>
 __device__ __forceinline__ void mac_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh,
                                          const int* __restrict__ gnbr, const MacWalk& it, int64_t wc) {
-    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
     if (it.e < 0) return;
-    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NW) + wc;
+    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NWS) + wc;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NW);
+    for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NWS);
 }
 
 template <typename T>
@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
                                                                    const int* __restrict__ gnbr, int n_groups,
                                                                    int groups_per_cta) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     for (int i = tid; i < 343 * 32; i += 32 * kMacWarps) {
         const int d = i >> 5, lane = i & 31;
         const int64_t w = w0 + lane;
-        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NW + w) : czero<T>();
+        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
     }
     __syncthreads();
     const int g0 = blockIdx.x * groups_per_cta;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
         if (!more || nxt.g != cur.g) {
             if (w < NW) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NW + w] = acc[c];
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NWS + w] = acc[c];
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
@@ -354,11 +355,239 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
         if (!more || nxt.g != cur.g) {
             if (w < NW) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NW + w] = acc[c];
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NWS + w] = acc[c];
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
         }
+        if (!more) break;
+        cur = nxt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level-0 near-field products, pipelined form.  Same work as k_mac_level0; the
+// 4^3 source blocks around the group are taken in 8 half-planes (fixed tz,
+// two ty rows, four tx) and the 8 spectra of the next half-plane are loaded
+// while the products of the current one run, so loads stay in flight with
+// few registers.  S is a template parameter so every offset is a constant.
+template <typename T, int S>
+__device__ __forceinline__ void mac0_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh, const int (&q)[27],
+                                          int step, int64_t w) {
+    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
+    const int tz = step / 2 - 1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int tx = (k & 3) - 1, ty = 2 * (step & 1) - 1 + (k >> 2);
+        const int ex = tx < 0 ? -1 : tx >> 1, ey = ty < 0 ? -1 : ty >> 1, ez = tz < 0 ? -1 : tz >> 1;
+        const int qq = q[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+        const int cs = (tx - 2 * ex) + 2 * (ty - 2 * ey) + 4 * (tz - 2 * ez);
+        F[k] = qq >= 0 ? ldg_cx(fh + (int64_t(qq) * 8 + cs) * NWS + w) : czero<T>();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void mac0_block(cx<T> (&acc)[8], const cx<T> (&F)[8], const cx<T> (&k)[27], int step) {
+    const int tz = step / 2 - 1;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const int tx = (kk & 3) - 1, ty = 2 * (step & 1) - 1 + (kk >> 2);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int dx = tx - (c & 1), dy = ty - ((c >> 1) & 1), dz = tz - (c >> 2);
+            if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+            acc[c] = cmac(acc[c], F[kk], k[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
+        }
+    }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256, 2) k_mac_level0_pipe(const cx<T>* __restrict__ fh,
+                                                            const cx<T>* __restrict__ kh,
+                                                            cx<T>* __restrict__ uh,
+                                                            const int* __restrict__ gnbr, int n_groups) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
+    const int64_t w = int64_t(blockIdx.y) * 32 + threadIdx.x;
+    const int g = blockIdx.x * blockDim.y + threadIdx.y;
+    if (g >= n_groups || w >= NW) return;
+    int q[27];
+#pragma unroll
+    for (int e = 0; e < 27; ++e) q[e] = __ldg(gnbr + int64_t(g) * 27 + e);
+    cx<T> Fa[8], Fb[8];
+    mac0_load<T, S>(Fa, fh, q, 0, w);
+    cx<T> k[27];
+#pragma unroll
+    for (int d = 0; d < 27; ++d) k[d] = ldg_cx(kh + d * NWS + w);
+    cx<T> acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
+#pragma unroll
+    for (int step = 0; step < 8; step += 2) {
+        mac0_load<T, S>(Fb, fh, q, step + 1, w);
+        mac0_block(acc, Fa, k, step);
+        if (step + 2 < 8) mac0_load<T, S>(Fa, fh, q, step + 2, w);
+        mac0_block(acc, Fb, k, step + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NWS + w] = acc[c];
+}
+
+// ---------------------------------------------------------------------------
+// Interaction-list products with two frequencies per thread: 128-bit loads of
+// source spectra and coefficients, half the load and address instructions per
+// FMA of k_mac_interval.  A CTA of kMac2Warps warps covers 64 frequencies; the
+// 343 coefficient rows of those frequencies fill shared memory (176 KB FP32),
+// so one CTA runs per SM.
+constexpr int kMac2Warps = 16;
+
+template <typename T>
+struct cx2 {
+    cx<T> a, b;
+};
+
+template <typename T>
+__device__ __forceinline__ cx2<T> ld2(const cx<T>* p) {
+    cx2<T> r;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        r.a = {v.x, v.y};
+        r.b = {v.z, v.w};
+    } else {
+        r.a = ldg_cx(p);
+        r.b = ldg_cx(p + 1);
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ cx2<T> lds2(const cx<T>* p) {
+    cx2<T> r;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        r.a = {v.x, v.y};
+        r.b = {v.z, v.w};
+    } else {
+        r.a = p[0];
+        r.b = p[1];
+    }
+    return r;
+}
+
+struct MacWalk2 {
+    int g, e;
+    unsigned mask;
+};
+
+__device__ __forceinline__ bool mac2_next(MacWalk2& it, const int* __restrict__ gnbr, int g1) {
+    if (it.mask) {
+        it.e = __ffs(it.mask) - 1;
+        it.mask &= it.mask - 1;
+        return true;
+    }
+    it.g += kMac2Warps;
+    if (it.g >= g1) return false;
+    it.mask = nbr_mask(gnbr, it.g);
+    if (it.mask) {
+        it.e = __ffs(it.mask) - 1;
+        it.mask &= it.mask - 1;
+    } else {
+        it.e = -1;
+    }
+    return true;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void mac2_load(cx2<T> (&F)[8], const cx<T>* __restrict__ fh,
+                                          const int* __restrict__ gnbr, const MacWalk2& it, int64_t wc) {
+    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
+    if (it.e < 0) return;
+    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NWS) + wc;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c] = ld2(src + c * NWS);
+}
+
+template <typename T>
+__device__ __forceinline__ void mac2_block(cx2<T> (&acc)[8], const cx2<T> (&F)[8], const cx<T>* __restrict__ sk,
+                                           int e) {
+    const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
+    const cx<T>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 64 + 2 * threadIdx.x;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const cx2<T> kk = lds2(kb + (dx + 7 * dy + 49 * dz) * 64);
+#pragma unroll
+                for (int ct = 0; ct < 8; ++ct) {
+                    const int cx_ = (ct & 1) + dx, cy_ = ((ct >> 1) & 1) + dy, cz_ = (ct >> 2) + dz;
+                    if (cx_ < 0 || cx_ > 1 || cy_ < 0 || cy_ > 1 || cz_ < 0 || cz_ > 1) continue;
+                    const int cs = cx_ + 2 * cy_ + 4 * cz_;
+                    acc[ct].a = cmac(acc[ct].a, F[cs].a, kk.a);
+                    acc[ct].b = cmac(acc[ct].b, F[cs].b, kk.b);
+                }
+            }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void mac2_store(cx2<T> (&acc)[8], cx<T>* __restrict__ uh, int g, int64_t w) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        cx<T>* o = uh + (int64_t(g) * 8 + c) * NWS + w;
+        if (w < NW) o[0] = acc[c].a;
+        if (w + 1 < NW) o[1] = acc[c].b;
+        acc[c].a = czero<T>();
+        acc[c].b = czero<T>();
+    }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T>* __restrict__ fh,
+                                                                     const cx<T>* __restrict__ kh,
+                                                                     cx<T>* __restrict__ uh,
+                                                                     const int* __restrict__ gnbr, int n_groups,
+                                                                     int groups_per_cta) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][64]
+    const int64_t w0 = int64_t(blockIdx.y) * 64;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < 343 * 64; i += 32 * kMac2Warps) {
+        const int d = i >> 6, lane = i & 63;
+        const int64_t w = w0 + lane;
+        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
+    }
+    __syncthreads();
+    const int g0 = blockIdx.x * groups_per_cta;
+    const int g1 = min(n_groups, g0 + groups_per_cta);
+    const int64_t w = w0 + 2 * threadIdx.x;
+    // the pair (w, w+1) is read as one 16-byte vector; w is even and the
+    // spectrum stride NWS is a multiple of 32, so the vector is aligned; past
+    // the end of the spectrum the read is clamped into the padded stride
+    const int64_t wc = w < NWS - 2 ? w : NWS - 2;
+    MacWalk2 cur{g0 + int(threadIdx.y) - kMac2Warps, -1, 0u};
+    if (!mac2_next(cur, gnbr, g1)) return;
+    cx2<T> Fa[8], Fb[8], acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = {czero<T>(), czero<T>()};
+    mac2_load<T, S>(Fa, fh, gnbr, cur, wc);
+    while (true) {
+        MacWalk2 nxt = cur;
+        bool more = mac2_next(nxt, gnbr, g1);
+        if (more) mac2_load<T, S>(Fb, fh, gnbr, nxt, wc);
+        if (cur.e >= 0) mac2_block(acc, Fa, sk, cur.e);
+        if (!more || nxt.g != cur.g) mac2_store<T, S>(acc, uh, cur.g, w);
+        if (!more) break;
+        cur = nxt;
+        nxt = cur;
+        more = mac2_next(nxt, gnbr, g1);
+        if (more) mac2_load<T, S>(Fa, fh, gnbr, nxt, wc);
+        if (cur.e >= 0) mac2_block(acc, Fb, sk, cur.e);
+        if (!more || nxt.g != cur.g) mac2_store<T, S>(acc, uh, cur.g, w);
         if (!more) break;
         cur = nxt;
     }
@@ -592,50 +821,81 @@ cudaError_t Launch<T>::c2r(int S, int n_out, const void* spec, const C2RItem* it
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr,
-                                  int n_groups, int S, cudaStream_t st) {
+template <typename T, int S>
+static cudaError_t launch_mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
+                                     int variant, cudaStream_t st) {
     if (n_groups == 0) return cudaSuccess;
-    const int64_t NW = nw_of(S);
+    const int64_t NW = nw_of(S), NWS = nws_of(S);
     const int G = 8;
     dim3 block(32, G), grid((n_groups + G - 1) / G, unsigned((NW + 31) / 32));
-    dev::k_mac_level0<T><<<grid, block, 0, st>>>(static_cast<const dev::cx<T>*>(fh),
-                                                 static_cast<const dev::cx<T>*>(kh),
-                                                 static_cast<dev::cx<T>*>(uh), gnbr, n_groups, NW);
+    const auto* f = static_cast<const dev::cx<T>*>(fh);
+    const auto* k = static_cast<const dev::cx<T>*>(kh);
+    auto* u = static_cast<dev::cx<T>*>(uh);
+    if (variant == 1) dev::k_mac_level0<T><<<grid, block, 0, st>>>(f, k, u, gnbr, n_groups, NW, NWS);
+    else dev::k_mac_level0_pipe<T, S><<<grid, block, 0, st>>>(f, k, u, gnbr, n_groups);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
+                                  int S, int variant, cudaStream_t st) {
+    switch (S) {
+        case 8: return launch_mac_level0<T, 8>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 16: return launch_mac_level0<T, 16>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 32: return launch_mac_level0<T, 32>(fh, kh, uh, gnbr, n_groups, variant, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int S>
 static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
-                                       cudaStream_t st) {
+                                       int variant, cudaStream_t st) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    const auto* f = static_cast<const dev::cx<T>*>(fh);
+    const auto* k = static_cast<const dev::cx<T>*>(kh);
+    auto* u = static_cast<dev::cx<T>*>(uh);
+    // groups per CTA: at least one per warp, and enough CTAs for ~4 waves;
+    // several groups per warp even out uneven neighbour counts
+    auto groups_per_cta = [&](int warps, int per_sm, int64_t nchunks) {
+        int per = warps;
+        while (per < n_groups && int64_t((n_groups + 2 * per - 1) / (2 * per)) * nchunks >= 4 * per_sm * 152)
+            per *= 2;
+        return per;
+    };
+    if (variant == 2) {
+        const size_t smem = sizeof(dev::cx<T>) * 343 * 64;
+        auto kern = dev::k_mac_interval2<T, S>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        if (n_groups == 0) return cudaSuccess;
+        const int64_t nchunks = (NW + 63) / 64;
+        const int per = groups_per_cta(dev::kMac2Warps, 1, nchunks);
+        dim3 block(32, dev::kMac2Warps), grid((n_groups + per - 1) / per, unsigned(nchunks));
+        kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
-    auto k = dev::k_mac_interval<T, S>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    auto kern = dev::k_mac_interval<T, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (n_groups == 0) return cudaSuccess;
-    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
-    const int nchunks = int((NW + 31) / 32);
-    // groups per CTA: at least one per warp, and enough CTAs for ~4 waves of
-    // two CTAs per SM; several groups per warp even out uneven neighbour counts
-    int per = dev::kMacWarps;
-    const int per_sm = sizeof(T) == 4 ? 2 : 1;
-    while (per < n_groups && int64_t((n_groups + 2 * per - 1) / (2 * per)) * nchunks >= 4 * per_sm * 152) per *= 2;
-    dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, nchunks);
-    k<<<grid, block, smem, st>>>(static_cast<const dev::cx<T>*>(fh), static_cast<const dev::cx<T>*>(kh),
-                                 static_cast<dev::cx<T>*>(uh), gnbr, n_groups, per);
+    const int64_t nchunks = (NW + 31) / 32;
+    const int per = groups_per_cta(dev::kMacWarps, sizeof(T) == 4 ? 2 : 1, nchunks);
+    dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
+    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
-                                    int n_groups, int S, cudaStream_t st) {
+                                    int n_groups, int S, int variant, cudaStream_t st) {
     switch (S) {
-        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, n_groups, st);
-        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, n_groups, st);
-        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, n_groups, st);
-        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, n_groups, st);
-        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, n_groups, st);
-        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, n_groups, st);
+        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, n_groups, variant, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -50,6 +50,10 @@ inline int s_level0(int n_b) { return 2 * n_b; }
 int s_interval(int n_b);
 inline int nx_of(int S) { return S / 2 + 1; }
 inline int64_t nw_of(int S) { return int64_t(nx_of(S)) * S * S; }
+// Stride between consecutive spectra in memory: NW rounded up to 32 entries,
+// so every spectrum starts 256-byte aligned (FP32) and vector loads of
+// frequency pairs stay aligned whatever the parity of NW.
+inline int64_t nws_of(int S) { return (nw_of(S) + 31) / 32 * 32; }
 
 // ---- kernel-side parameter blocks ----
 struct R2CItem { int src; int dst; };      // source index -> spectrum slot
@@ -67,10 +71,11 @@ struct Launch {
     static cudaError_t c2r(int S, int n_out, const void* spec, const C2RItem* items, int n_items,
                            T* dst, int64_t dst_stride, const T* add, int add_n, int64_t add_stride,
                            cudaStream_t st);
+    // variant: 0/2 default form, 1 the earlier form (kept for comparison)
     static cudaError_t mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr,
-                                  int n_groups, int S, cudaStream_t st);
+                                  int n_groups, int S, int variant, cudaStream_t st);
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
-                                    int n_groups, int S, cudaStream_t st);
+                                    int n_groups, int S, int variant, cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,
                            const int* child_index, const int* parent_slot, int n_parents,

@@ -140,19 +140,22 @@ lgf_status load_kernel(DeviceState& st, int n_b, int prec) {
 
 // spec[b][w] <- spec[b][w] * kh[w] (the single product of Eq. alg_mult for a
 // block whose only near neighbour is itself)
+// (block spectra are NWS apart; entries past NW are padding and stay as they are)
 template <typename T>
 __global__ void k_mul_spectrum(dev::cx<T>* __restrict__ spec, const dev::cx<T>* __restrict__ kh, int64_t NW,
-                               int64_t total) {
+                               int64_t NWS, int64_t total) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
          i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t w = i % NWS;
+        if (w >= NW) continue;
         const dev::cx<T> f = spec[i];
-        spec[i] = dev::cmac(dev::czero<T>(), f, dev::ldg_cx(kh + i % NW));
+        spec[i] = dev::cmac(dev::czero<T>(), f, dev::ldg_cx(kh + w));
     }
 }
 
 template <typename T, int S, int NB>
 lgf_status run(DeviceState& st, const T* f, T* u, int64_t n, int prec, cudaStream_t stream) {
-    const int64_t NW = nw_of(S);
+    const int64_t NW = nw_of(S), NWS = nws_of(S);
     auto* spec = reinterpret_cast<dev::cx<T>*>(st.base + kSpecOffset);
     const auto* kh = reinterpret_cast<const dev::cx<T>*>(st.base + kernel_offset(NB, prec));
     const auto* r2c = reinterpret_cast<const R2CItem*>(st.base + kKernelRegion);
@@ -160,9 +163,9 @@ lgf_status run(DeviceState& st, const T* f, T* u, int64_t n, int prec, cudaStrea
     const int64_t b3 = int64_t(NB) * NB * NB;
     cudaError_t e = launch_r2c<T, S, NB>(f, b3, r2c, int(n), spec, stream);
     if (e != cudaSuccess) return cuda_err(e, "forward FFT");
-    const int64_t total = n * NW;
+    const int64_t total = n * NWS;
     const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 16));
-    k_mul_spectrum<T><<<grid, 256, 0, stream>>>(spec, kh, NW, total);
+    k_mul_spectrum<T><<<grid, 256, 0, stream>>>(spec, kh, NW, NWS, total);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "spectral product");
     e = launch_c2r<T, S, NB>(spec, c2r, int(n), u, b3, nullptr, 0, 0, stream);
     if (e != cudaSuccess) return cuda_err(e, "inverse FFT");
@@ -177,7 +180,7 @@ using namespace lgf;
 extern "C" lgf_status lgf_noalloc_max_blocks(int32_t n_b, int32_t precision, int64_t* max_blocks) {
     if (!max_blocks || nb_index(n_b) < 0 || (precision != LGF_FP32 && precision != LGF_FP64))
         return fail(LGF_ERR_INVALID_ARG, "lgf_noalloc_max_blocks: need n_b in {4, 8, 16}, a precision and an output");
-    const size_t per = size_t(nw_of(2 * n_b)) * 2 * (precision == LGF_FP64 ? 8 : 4);
+    const size_t per = size_t(nws_of(2 * n_b)) * 2 * (precision == LGF_FP64 ? 8 : 4);
     *max_blocks = std::min<int64_t>(kMaxItems, int64_t((kNoAllocScratchBytes - kSpecOffset) / per));
     return ok();
 }

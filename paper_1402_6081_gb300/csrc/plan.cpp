@@ -165,8 +165,8 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int 
     const int V = near ? 2 * n_b - 1 : 4 * n_b;
     auto tab = green_abs_table(h, V);
     const int nd = near ? 27 : 343;
-    const int64_t NW = nw_of(S);
-    std::vector<std::complex<double>> all(size_t(nd) * NW, 0.0);
+    const int64_t NW = nw_of(S), NWS = nws_of(S);
+    std::vector<std::complex<double>> all(size_t(nd) * NWS, 0.0);
     std::vector<int> todo;
     for (int id = 0; id < nd; ++id) {
         const int r = near ? 3 : 7, o = near ? 1 : 3;
@@ -182,14 +182,15 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int 
                 const int id = todo[t];
                 const int r = near ? 3 : 7, o = near ? 1 : 3;
                 const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
-                kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(id) * NW]);
+                kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(id) * NWS]);
             }
         });
     for (auto& t : th) t.join();
     auto e = std::make_shared<SpecEntry>();
     e->device = device;
     const size_t elem = prec == LGF_FP64 ? sizeof(double) : sizeof(float);
-    e->bytes = size_t(nd) * NW * 2 * elem;
+    e->bytes = size_t(nd) * NWS * 2 * elem;
+    (void)NW;
     cudaError_t ce = cudaMalloc(&e->ptr, e->bytes);
     if (ce != cudaSuccess) {
         e->ptr = nullptr;
@@ -198,7 +199,7 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int 
     if (prec == LGF_FP64) {
         ce = cudaMemcpy(e->ptr, all.data(), e->bytes, cudaMemcpyHostToDevice);
     } else {
-        std::vector<float> f(size_t(nd) * NW * 2);
+        std::vector<float> f(size_t(nd) * NWS * 2);
         for (size_t i = 0; i < all.size(); ++i) {
             f[2 * i] = float(all[i].real());
             f[2 * i + 1] = float(all[i].imag());
@@ -275,6 +276,7 @@ struct lgf_plan_s {
     int n_b = 0, n_I = 0, L = 0, n_max = 0, prec = LGF_FP32;
     int64_t n_blocks = 0, n_points = 0;
     int S0 = 0, SI = 0, Lmac = 0;
+    int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     std::vector<lgf::DevLevel> lev;
     std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
     void* W = nullptr;                  // device copy (unused by the kernels, kept for tools)
@@ -467,9 +469,9 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         lgf_status s;
         if (D.m2l) {
             const int S = l == 0 ? P->S0 : P->SI;
-            const size_t NW = size_t(nw_of(S));
-            if ((s = dalloc(P, slots * NW * cplx, &D.fh, true)) != LGF_OK) return s;
-            if ((s = dalloc(P, slots * NW * cplx, &D.uh, false)) != LGF_OK) return s;
+            const size_t NWS = size_t(nws_of(S));
+            if ((s = dalloc(P, slots * NWS * cplx, &D.fh, true)) != LGF_OK) return s;
+            if ((s = dalloc(P, slots * NWS * cplx, &D.uh, false)) != LGF_OK) return s;
             std::vector<int> gn(size_t(D.n_groups) * 27, -1);
             for (int g = 0; g < D.n_groups; ++g)
                 for (int e = 0; e < 27; ++e) {
@@ -612,14 +614,15 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     }
     // Step 2: level interactions
     e = timed(P, "mac_level0", st, [&] {
-        return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0, st);
+        return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
+                              P->near_kernel, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "near-field products");
     for (int l = 1; l <= P->Lmac; ++l) {
         DevLevel& D = lev[size_t(l)];
         if (!D.m2l) continue;
         e = timed(P, l == 1 ? "mac_interval_l1" : "mac_interval_l2plus", st, [&] {
-            return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, st);
+            return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, P->interval_kernel, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
     }
@@ -717,6 +720,12 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
                                                  std::to_string(opts->fft_size_interval) +
                                                  " is not built for n_b = " + std::to_string(n_b));
         P->SI = opts->fft_size_interval;
+    }
+    if (opts) {
+        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 2)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel / interval_kernel must be 0, 1 or 2");
+        P->near_kernel = opts->near_kernel;
+        P->interval_kernel = opts->interval_kernel;
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;

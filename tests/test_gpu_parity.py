@@ -138,6 +138,30 @@ def test_deep_tree_nb4_five_levels():
     check(m)
 
 
+_variant_problem = None
+
+
+@pytest.mark.parametrize("S", [33, 34, 36])
+@pytest.mark.parametrize("near,interval", [(1, 1), (2, 2), (2, 1), (1, 2)])
+def test_kernel_variants_and_fft_lengths(S, near, interval):
+    # every product-kernel variant and interval FFT length computes the same
+    # method (6^3 blocks of 16^3, 3 levels: level 2 has an interaction list)
+    global _variant_problem
+    if _variant_problem is None:
+        _variant_problem = W.torus_box(seed=2, nb=6, n_b=16, radius=30.0, sigma=5.0, n_levels=3)
+    p = _variant_problem
+    ref = oracle_u(p)
+    for prec, tol in ((lgfm.LGF_FP64, TOL64), (lgfm.LGF_FP32, TOL32)):
+        dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=S,
+                        near_kernel=near, interval_kernel=interval)
+        u = s(torch.from_numpy(p.f).to(dt).cuda())
+        torch.cuda.synchronize()
+        err = fmm.rel_linf(u.double().cpu().numpy(), ref)
+        s.close()
+        assert err <= tol, (prec, err)
+
+
 def test_plan_errors():
     b = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0]], dtype=np.int32)
     with pytest.raises(lgfm.LgfError) as e:
