@@ -97,6 +97,7 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      unrolled 4^3-source form, 2 = half-plane pipelined form
  *   interval_kernel    product kernel of levels >= 1: 0 = default, 1 = one
  *                      frequency per thread, 2 = two frequencies per thread
+ *                      (FP32 only; FP64 plans use 1)
  * All variants compute the same sums (Eq. alg_mult) in the same order per
  * target; they differ only in scheduling.
  */

@@ -862,7 +862,9 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
             per *= 2;
         return per;
     };
-    if (variant == 2) {
+    // two frequencies per thread need 343 x 64 coefficients in shared memory:
+    // 176 KB in FP32, too much in FP64, which keeps the one-frequency form
+    if (variant == 2 && sizeof(T) == 4) {
         const size_t smem = sizeof(dev::cx<T>) * 343 * 64;
         auto kern = dev::k_mac_interval2<T, S>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
