@@ -96,8 +96,9 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *   near_kernel        product kernel of level 0: 0 = default, 1 = fully
  *                      unrolled 4^3-source form, 2 = half-plane pipelined form
  *   interval_kernel    product kernel of levels >= 1: 0 = default, 1 = one
- *                      frequency per thread, 2 = two frequencies per thread
- *                      (FP32 only; FP64 plans use 1)
+ *                      frequency per thread, 2 = two frequencies per thread,
+ *                      3 = two sibling groups per warp sharing coefficient
+ *                      loads (2 and 3: FP32 only; FP64 plans use 1)
  * All variants compute the same sums (Eq. alg_mult) in the same order per
  * target; they differ only in scheduling.
  */

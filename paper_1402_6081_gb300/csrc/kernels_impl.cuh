@@ -594,6 +594,117 @@ __global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T
 }
 
 // ---------------------------------------------------------------------------
+// Interaction-list products, two groups per warp.  The bound of the
+// one-group form is the shared-memory/L1 data path: 27 coefficient loads per
+// 64 products.  Here a warp walks two Morton-adjacent groups A, B together,
+// over the union of their neighbour offsets e; the 27 coefficients of e are
+// loaded once and applied to A's and B's source blocks (each only if that
+// group has neighbour e, a warp-uniform test), which halves coefficient
+// traffic per product.  One CTA of kMacPWarps warps per SM (FP32 registers).
+constexpr int kMacPWarps = 8;
+
+template <typename T, int S>
+__device__ __forceinline__ void macp_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh, int q, int64_t wc) {
+    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
+    const cx<T>* src = fh + int64_t(q) * (8 * NWS) + wc;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NWS);
+}
+
+template <typename T>
+__device__ __forceinline__ void macp_coef(cx<T> (&kk)[27], const cx<T>* __restrict__ sk, int e) {
+    const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
+    const cx<T>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 32 + threadIdx.x;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
+}
+
+template <typename T>
+__device__ __forceinline__ void macp_block(cx<T> (&acc)[8], const cx<T> (&F)[8], const cx<T> (&kk)[27]) {
+#pragma unroll
+    for (int ct = 0; ct < 8; ++ct)
+#pragma unroll
+        for (int cs = 0; cs < 8; ++cs) {
+            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
+            acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
+        }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const cx<T>* __restrict__ fh,
+                                                                         const cx<T>* __restrict__ kh,
+                                                                         cx<T>* __restrict__ uh,
+                                                                         const int* __restrict__ gnbr,
+                                                                         int n_groups, int groups_per_cta) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
+    const int64_t w0 = int64_t(blockIdx.y) * 32;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < 343 * 32; i += 32 * kMacPWarps) {
+        const int d = i >> 5, lane = i & 31;
+        const int64_t w = w0 + lane;
+        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
+    }
+    __syncthreads();
+    const int g0 = blockIdx.x * groups_per_cta;
+    const int g1 = min(n_groups, g0 + groups_per_cta);
+    const int64_t w = w0 + threadIdx.x;
+    const int64_t wc = w < NW ? w : NW - 1;
+    for (int ga = g0 + 2 * int(threadIdx.y); ga < g1; ga += 2 * kMacPWarps) {
+        const int gb = ga + 1 < g1 ? ga + 1 : -1;
+        const unsigned ma = nbr_mask(gnbr, ga);
+        const unsigned mb = gb >= 0 ? nbr_mask(gnbr, gb) : 0u;
+        unsigned mask = ma | mb;
+        cx<T> accA[8], accB[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            accA[c] = czero<T>();
+            accB[c] = czero<T>();
+        }
+        if (mask) {
+            int e = __ffs(mask) - 1;
+            mask &= mask - 1;
+            cx<T> FA[8], FB[8];
+            if ((ma >> e) & 1) macp_load<T, S>(FA, fh, __ldg(gnbr + int64_t(ga) * 27 + e), wc);
+            if ((mb >> e) & 1) macp_load<T, S>(FB, fh, __ldg(gnbr + int64_t(gb) * 27 + e), wc);
+            while (true) {
+                const int en = mask ? __ffs(mask) - 1 : -1;
+                mask &= mask - 1;
+                cx<T> NA[8], NB[8];
+                if (en >= 0 && ((ma >> en) & 1)) macp_load<T, S>(NA, fh, __ldg(gnbr + int64_t(ga) * 27 + en), wc);
+                if (en >= 0 && ((mb >> en) & 1)) macp_load<T, S>(NB, fh, __ldg(gnbr + int64_t(gb) * 27 + en), wc);
+                cx<T> kk[27];
+                macp_coef(kk, sk, e);
+                if ((ma >> e) & 1) macp_block(accA, FA, kk);
+                if ((mb >> e) & 1) macp_block(accB, FB, kk);
+                if (en < 0) break;
+                e = en;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    FA[c] = NA[c];
+                    FB[c] = NB[c];
+                }
+            }
+        }
+        if (w < NW) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) uh[(int64_t(ga) * 8 + c) * NWS + w] = accA[c];
+            if (gb >= 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) uh[(int64_t(gb) * 8 + c) * NWS + w] = accB[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Reg (Eq. alg_reg) and Interp (Eq. alg_interp): tensor products of the 1D
 // matrices W[c][i][p] (weight of parent node p for child node i).  The two
 // n_I x n_I matrices travel as a by-value kernel parameter, so with every loop
@@ -862,6 +973,18 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
             per *= 2;
         return per;
     };
+    if (variant == 3 && sizeof(T) == 4) {
+        const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
+        auto kern = dev::k_mac_interval_pair<T, S>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        if (n_groups == 0) return cudaSuccess;
+        const int64_t nchunks = (NW + 31) / 32;
+        int per = groups_per_cta(2 * dev::kMacPWarps, 1, nchunks);
+        dim3 block(32, dev::kMacPWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
+        kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
+        return cudaGetLastError();
+    }
     // two frequencies per thread need 343 x 64 coefficients in shared memory:
     // 176 KB in FP32, too much in FP64, which keeps the one-frequency form
     if (variant == 2 && sizeof(T) == 4) {

@@ -722,8 +722,8 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
         P->SI = opts->fft_size_interval;
     }
     if (opts) {
-        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 2)
-            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel / interval_kernel must be 0, 1 or 2");
+        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 3)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..3");
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
     }

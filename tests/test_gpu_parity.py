@@ -142,7 +142,7 @@ _variant_problem = None
 
 
 @pytest.mark.parametrize("S", [33, 34, 36])
-@pytest.mark.parametrize("near,interval", [(1, 1), (2, 2), (2, 1), (1, 2)])
+@pytest.mark.parametrize("near,interval", [(1, 1), (2, 2), (2, 1), (1, 2), (2, 3)])
 def test_kernel_variants_and_fft_lengths(S, near, interval):
     # every product-kernel variant and interval FFT length computes the same
     # method (6^3 blocks of 16^3, 3 levels: level 2 has an interaction list)
