@@ -37,38 +37,50 @@ __device__ __forceinline__ cx<double> ldg_cx<double>(const cx<double>* p) {
 
 constexpr int kFftThreads = 256;
 
+// Shared-memory footprint of the FFT kernels (bytes): the partially
+// transformed cube with an odd row pitch, plus the staged real cube.
+template <typename T, int S, int N>
+__host__ __device__ constexpr size_t fft_smem_bytes() {
+    return sizeof(cx<T>) * size_t(N) * S * ((S / 2 + 1) | 1) + sizeof(T) * size_t(N) * N * (N | 1);
+}
+
 // ---------------------------------------------------------------------------
 // Padded R2C (Eq. alg_upfft): an NIN^3 real cube, zero-padded to S^3, to its
-// half spectrum.  One CTA per item; the partially transformed cube stays in
-// shared memory as B[(z*S + ky)*NX + kx], z < NIN (only NIN z-planes are
-// non-zero until the last pass, which goes straight to global memory).
+// half spectrum.  One CTA per item.  The input cube is first copied into
+// shared memory with coalesced loads (rows of odd pitch RS).  The partially
+// transformed cube stays in shared memory as B[(z*S + ky)*NXP + kx], z < NIN,
+// NXP = NX rounded up to odd, so one-line-per-thread passes are free of bank
+// conflicts; the last pass goes straight to global memory.
 template <typename T, int S, int NIN>
 __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, int64_t src_stride,
                                                      const R2CItem* __restrict__ items,
                                                      cx<T>* __restrict__ spec) {
-    constexpr int NX = S / 2 + 1;
+    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NIN | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
+    T* X = reinterpret_cast<T*>(B + NIN * S * NXP);
     const R2CItem it = items[blockIdx.x];
     const T* in = src + int64_t(it.src) * src_stride;
     cx<T>* out = spec + int64_t(it.dst) * NWS;
 
-    // x pass: two real lines per complex transform
+    for (int i = threadIdx.x; i < NIN * NIN * NIN; i += blockDim.x) X[(i / NIN) * RS + i % NIN] = in[i];
+    __syncthreads();
+    // x pass: lines l and l + NP (rows of the (y, z) plane) as one complex transform
     constexpr int NL = NIN * NIN, NP = (NL + 1) / 2;
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-        const int l0 = 2 * p, l1 = 2 * p + 1;
+        const int l0 = p, l1 = p + NP;
         const bool has1 = l1 < NL;
-        const T* r0 = in + int64_t(l0) * NIN;
-        const T* r1 = in + int64_t(has1 ? l1 : l0) * NIN;
+        const T* r0 = X + l0 * RS;
+        const T* r1 = X + (has1 ? l1 : l0) * RS;
         cx<T> z[S];
 #pragma unroll
         for (int x = 0; x < S; ++x)
             z[x] = x < NIN ? cx<T>{r0[x], has1 ? r1[x] : T(0)} : czero<T>();
         fft<S, S, -1, NIN>(z);
         const int y0 = l0 % NIN, z0 = l0 / NIN, y1 = l1 % NIN, z1 = l1 / NIN;
-        cx<T>* d0 = B + (z0 * S + y0) * NX;
-        cx<T>* d1 = B + (z1 * S + y1) * NX;
+        cx<T>* d0 = B + (z0 * S + y0) * NXP;
+        cx<T>* d1 = B + (z1 * S + y1) * NXP;
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
             const cx<T> a = z[k], b = z[(S - k) % S];
@@ -80,21 +92,22 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
     // y pass: lines (kx, z), in place within the column
     for (int l = threadIdx.x; l < NX * NIN; l += blockDim.x) {
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * S * NX + kx;
+        cx<T>* col = B + zz * S * NXP + kx;
         cx<T> v[S];
 #pragma unroll
-        for (int y = 0; y < S; ++y) v[y] = y < NIN ? col[y * NX] : czero<T>();
+        for (int y = 0; y < S; ++y) v[y] = y < NIN ? col[y * NXP] : czero<T>();
         fft<S, S, -1, NIN>(v);
 #pragma unroll
-        for (int y = 0; y < S; ++y) col[y * NX] = v[y];
+        for (int y = 0; y < S; ++y) col[y * NXP] = v[y];
     }
     __syncthreads();
     // z pass: lines (kx, ky), results to global (coalesced across the CTA)
     for (int l = threadIdx.x; l < NX * S; l += blockDim.x) {
-        const cx<T>* col = B + l;
+        const int kx = l % NX, ky = l / NX;
+        const cx<T>* col = B + ky * NXP + kx;
         cx<T> v[S];
 #pragma unroll
-        for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * S * NX] : czero<T>();
+        for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * S * NXP] : czero<T>();
         fft<S, S, -1, NIN>(v);
 #pragma unroll
         for (int kz = 0; kz < S; ++kz) out[int64_t(kz) * S * NX + l] = v[kz];
@@ -105,52 +118,55 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
 // Truncated C2R (Eq. alg_dwfft): keep the first NOUT samples per axis.
 //   dst[item.dst*dst_stride + (z*NOUT + y)*NOUT + x] = v (+ add[item.aux*add_stride
 //   + (z*add_n + y)*add_n + x] when add != null and item.aux >= 0)
-// The 1/S^3 of the inverse transform is folded into the kernel spectra.
+// The 1/S^3 of the inverse transform is folded into the kernel spectra.  The
+// result cube is staged in shared memory (odd row pitch) and written with
+// coalesced stores.
 template <typename T, int S, int NOUT>
 __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ spec,
                                                      const C2RItem* __restrict__ items,
                                                      T* __restrict__ dst, int64_t dst_stride,
                                                      const T* __restrict__ add, int add_n,
                                                      int64_t add_stride) {
-    constexpr int NX = S / 2 + 1;
+    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NOUT | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
+    T* O = reinterpret_cast<T*>(B + NOUT * S * NXP);
     const C2RItem it = items[blockIdx.x];
     const cx<T>* in = spec + int64_t(it.src) * NWS;
 
     // z pass: lines (kx, ky); keep z < NOUT
     for (int l = threadIdx.x; l < NX * S; l += blockDim.x) {
+        const int kx = l % NX, ky = l / NX;
         cx<T> v[S];
 #pragma unroll
         for (int kz = 0; kz < S; ++kz) v[kz] = ldg_cx(in + int64_t(kz) * S * NX + l);
         fft<S, S, 1, S>(v);
+        cx<T>* col = B + ky * NXP + kx;
 #pragma unroll
-        for (int zz = 0; zz < NOUT; ++zz) B[zz * S * NX + l] = v[zz];
+        for (int zz = 0; zz < NOUT; ++zz) col[zz * S * NXP] = v[zz];
     }
     __syncthreads();
     // y pass: lines (kx, z < NOUT); keep y < NOUT
     for (int l = threadIdx.x; l < NX * NOUT; l += blockDim.x) {
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * S * NX + kx;
+        cx<T>* col = B + zz * S * NXP + kx;
         cx<T> v[S];
 #pragma unroll
-        for (int y = 0; y < S; ++y) v[y] = col[y * NX];
+        for (int y = 0; y < S; ++y) v[y] = col[y * NXP];
         fft<S, S, 1, S>(v);
 #pragma unroll
-        for (int y = 0; y < NOUT; ++y) col[y * NX] = v[y];
+        for (int y = 0; y < NOUT; ++y) col[y * NXP] = v[y];
     }
     __syncthreads();
-    // x pass: two Hermitian half-lines per complex inverse transform
+    // x pass: two Hermitian half-lines (rows l and l + NP) per complex inverse
     constexpr int NL = NOUT * NOUT, NP = (NL + 1) / 2;
-    T* out = dst + int64_t(it.dst) * dst_stride;
-    const T* ad = (add != nullptr && it.aux >= 0) ? add + int64_t(it.aux) * add_stride : nullptr;
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-        const int l0 = 2 * p, l1 = 2 * p + 1;
+        const int l0 = p, l1 = p + NP;
         const bool has1 = l1 < NL;
         const int y0 = l0 % NOUT, z0 = l0 / NOUT, y1 = l1 % NOUT, z1 = l1 / NOUT;
-        const cx<T>* a = B + (z0 * S + y0) * NX;
-        const cx<T>* b = B + ((has1 ? z1 : z0) * S + (has1 ? y1 : y0)) * NX;
+        const cx<T>* a = B + (z0 * S + y0) * NXP;
+        const cx<T>* b = B + ((has1 ? z1 : z0) * S + (has1 ? y1 : y0)) * NXP;
         cx<T> z[S];
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
@@ -163,15 +179,20 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
             if (k > 0 && S - k >= NX) z[S - k] = {A.x + Bk.y, Bk.x - A.y};
         }
         fft<S, S, 1, S>(z);
-        T* o0 = out + (z0 * NOUT + y0) * NOUT;
-        T* o1 = out + (z1 * NOUT + y1) * NOUT;
-        const T* a0 = ad ? ad + (z0 * add_n + y0) * add_n : nullptr;
-        const T* a1 = ad ? ad + (z1 * add_n + y1) * add_n : nullptr;
 #pragma unroll
         for (int x = 0; x < NOUT; ++x) {
-            o0[x] = a0 ? z[x].x + a0[x] : z[x].x;
-            if (has1) o1[x] = a1 ? z[x].y + a1[x] : z[x].y;
+            O[l0 * RS + x] = z[x].x;
+            if (has1) O[l1 * RS + x] = z[x].y;
         }
+    }
+    __syncthreads();
+    T* out = dst + int64_t(it.dst) * dst_stride;
+    const T* ad = (add != nullptr && it.aux >= 0) ? add + int64_t(it.aux) * add_stride : nullptr;
+    for (int i = threadIdx.x; i < NOUT * NOUT * NOUT; i += blockDim.x) {
+        const int x = i % NOUT, yz = i / NOUT;
+        T v = O[yz * RS + x];
+        if (ad) v += ad[((yz / NOUT) * add_n + yz % NOUT) * add_n + x];
+        out[i] = v;
     }
 }
 
@@ -239,8 +260,9 @@ constexpr int kMacWarps = 12;
 // g0 + warp, g0 + warp + kMacWarps, ... below g1, and for each group the
 // present neighbour groups e != 13 in increasing order.
 struct MacWalk {
-    int g, e;            // current pair (e < 0: group without neighbours)
-    unsigned mask;       // neighbours of g not yet visited
+    int g, e;            // current pair (g: position in the work order; e < 0: no neighbours)
+    int gid;             // group id at position g
+    unsigned mask;       // neighbours of gid not yet visited
 };
 
 __device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g) {
@@ -253,7 +275,8 @@ __device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g
 }
 
 // advance to the next pair; returns false past the warp's last group
-__device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gnbr, int g1) {
+__device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gnbr, const int* __restrict__ order,
+                                         int g1) {
     if (it.mask) {
         it.e = __ffs(it.mask) - 1;
         it.mask &= it.mask - 1;
@@ -261,7 +284,8 @@ __device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gn
     }
     it.g += kMacWarps;
     if (it.g >= g1) return false;
-    it.mask = nbr_mask(gnbr, it.g);
+    it.gid = __ldg(order + it.g);
+    it.mask = nbr_mask(gnbr, it.gid);
     if (it.mask) {
         it.e = __ffs(it.mask) - 1;
         it.mask &= it.mask - 1;
@@ -276,7 +300,7 @@ __device__ __forceinline__ void mac_load(cx<T> (&F)[8], const cx<T>* __restrict_
                                          const int* __restrict__ gnbr, const MacWalk& it, int64_t wc) {
     constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
     if (it.e < 0) return;
-    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NWS) + wc;
+    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.gid) * 27 + it.e)) * (8 * NWS) + wc;
 #pragma unroll
     for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NWS);
 }
@@ -304,11 +328,14 @@ __device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], 
         }
 }
 
+// Groups are visited in the plan's work order (sorted by neighbour count, so
+// the warps of one CTA carry similar work).
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_interval(const cx<T>* __restrict__ fh,
                                                                    const cx<T>* __restrict__ kh,
                                                                    cx<T>* __restrict__ uh,
-                                                                   const int* __restrict__ gnbr, int n_groups,
+                                                                   const int* __restrict__ gnbr,
+                                                                   const int* __restrict__ order, int n_groups,
                                                                    int groups_per_cta) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
@@ -326,8 +353,8 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
-    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0u};
-    if (!mac_next(cur, gnbr, g1)) return;
+    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0, 0u};
+    if (!mac_next(cur, gnbr, order, g1)) return;
     cx<T> Fa[8], Fb[8], acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
@@ -335,13 +362,13 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     // two pairs per trip so the prefetch buffers alternate without copies
     while (true) {
         MacWalk nxt = cur;
-        bool more = mac_next(nxt, gnbr, g1);
+        bool more = mac_next(nxt, gnbr, order, g1);
         if (more) mac_load<T, S>(Fb, fh, gnbr, nxt, wc);
         if (cur.e >= 0) mac_block(acc, Fa, sk, cur.e);
         if (!more || nxt.g != cur.g) {
             if (w < NW) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NWS + w] = acc[c];
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.gid) * 8 + c) * NWS + w] = acc[c];
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
@@ -349,13 +376,13 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
         if (!more) break;
         cur = nxt;
         nxt = cur;
-        more = mac_next(nxt, gnbr, g1);
+        more = mac_next(nxt, gnbr, order, g1);
         if (more) mac_load<T, S>(Fa, fh, gnbr, nxt, wc);
         if (cur.e >= 0) mac_block(acc, Fb, sk, cur.e);
         if (!more || nxt.g != cur.g) {
             if (w < NW) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.g) * 8 + c) * NWS + w] = acc[c];
+                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.gid) * 8 + c) * NWS + w] = acc[c];
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
@@ -883,8 +910,7 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
 template <typename T, int S, int NIN>
 static cudaError_t launch_r2c(const T* src, int64_t stride, const R2CItem* items, int n,
                               void* spec, cudaStream_t st) {
-    constexpr int NX = S / 2 + 1;
-    const size_t smem = sizeof(dev::cx<T>) * NIN * S * NX;
+    const size_t smem = dev::fft_smem_bytes<T, S, NIN>();
     auto k = dev::k_r2c<T, S, NIN>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -896,8 +922,7 @@ static cudaError_t launch_r2c(const T* src, int64_t stride, const R2CItem* items
 template <typename T, int S, int NOUT>
 static cudaError_t launch_c2r(const void* spec, const C2RItem* items, int n, T* dst, int64_t ds,
                               const T* add, int add_n, int64_t as, cudaStream_t st) {
-    constexpr int NX = S / 2 + 1;
-    const size_t smem = sizeof(dev::cx<T>) * NOUT * S * NX;
+    const size_t smem = dev::fft_smem_bytes<T, S, NOUT>();
     auto k = dev::k_c2r<T, S, NOUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -959,8 +984,8 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
 }
 
 template <typename T, int S>
-static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
-                                       int variant, cudaStream_t st) {
+static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
+                                       int n_groups, int variant, cudaStream_t st) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     const auto* f = static_cast<const dev::cx<T>*>(fh);
     const auto* k = static_cast<const dev::cx<T>*>(kh);
@@ -1007,20 +1032,20 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
     const int64_t nchunks = (NW + 31) / 32;
     const int per = groups_per_cta(dev::kMacWarps, sizeof(T) == 4 ? 2 : 1, nchunks);
     dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
-    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
+    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
+cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, cudaStream_t st) {
     switch (S) {
-        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, n_groups, variant, st);
+        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, order, n_groups, variant, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -74,7 +74,8 @@ struct Launch {
     // variant: 0/2 default form, 1 the earlier form (kept for comparison)
     static cudaError_t mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr,
                                   int n_groups, int S, int variant, cudaStream_t st);
-    static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr,
+    // order: the groups in work order (descending neighbour count)
+    static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,

@@ -256,6 +256,7 @@ struct DevLevel {
     void* ft = nullptr;
     void* ut = nullptr;
     int* gnbr = nullptr;
+    int* order = nullptr;      // groups sorted by descending neighbour count
     R2CItem* r2c = nullptr;
     int n_r2c = 0;
     C2RItem* c2r = nullptr;
@@ -293,6 +294,10 @@ struct lgf_plan_s {
     std::vector<const char*> ev_name;      // kernel name per recorded pair
     int ev_used = 0;
     int launches_last = 0;                 // kernels launched by the last solve
+    // the level-1 chain and the level >= 2 chain run on their own streams,
+    // forked from and joined into the caller's stream
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 
     ~lgf_plan_s() {
         int cur = 0;
@@ -303,6 +308,11 @@ struct lgf_plan_s {
         if (stage_f) cudaFree(stage_f);
         if (stage_u) cudaFree(stage_u);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaStream_t a : aux)
+            if (a) cudaStreamDestroy(a);
+        if (fork) cudaEventDestroy(fork);
+        for (cudaEvent_t j : join)
+            if (j) cudaEventDestroy(j);
         lev.clear();
         cudaSetDevice(cur);
     }
@@ -481,6 +491,15 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
                     if (it != L_.group_index.end()) gn[size_t(g) * 27 + e] = it->second;
                 }
             if ((s = upload(P, gn, &D.gnbr)) != LGF_OK) return s;
+            {
+                std::vector<int> cnt(size_t(D.n_groups), 0), ord(size_t(D.n_groups));
+                for (int g = 0; g < D.n_groups; ++g) {
+                    for (int e = 0; e < 27; ++e) cnt[size_t(g)] += gn[size_t(g) * 27 + e] >= 0;
+                    ord[size_t(g)] = g;
+                }
+                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cnt[size_t(a)] > cnt[size_t(b)]; });
+                if ((s = upload(P, ord, &D.order)) != LGF_OK) return s;
+            }
             std::vector<R2CItem> items;
             for (size_t i = 0; i < L_.iv.size(); ++i) {
                 const int slot = L_.slot(L_.iv[i]);
@@ -591,62 +610,101 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(P->Wd.data());
     else W = reinterpret_cast<const T*>(P->Wf.data());
     cudaError_t e;
-    // Step 1: upward pass
+    const int Lm = P->Lmac;
+    cudaStream_t s1 = P->aux[0], s2 = P->aux[1];
+    // fork: the other chains start after all prior work on the caller's stream
+    if (Lm >= 1) {
+        LGF_CUDA(cudaEventRecord(P->fork, st));
+        LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
+        if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
+    }
+    // ---- level 0 on the caller's stream: forward FFT, near-field products
     e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
     if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
-    for (int l = 1; l <= P->Lmac; ++l) {
-        DevLevel& D = lev[size_t(l)];
-        if (l >= 2) {
-            const bool from_blocks = l == 2;
-            e = timed(P, "reg", st, [&] {
-                return Lc::reg(nb, P->n_max, from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft),
-                               from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg, static_cast<T*>(D.ft), W, st);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "regularization");
-        }
-        if (D.m2l) {
-            e = timed(P, "r2c_interval", st, [&] {
-                return l == 1 ? Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, st)
-                              : Lc::r2c(P->SI, nI, static_cast<const T*>(D.ft), n3, D.r2c, D.n_r2c, D.fh, st);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
-        }
-    }
-    // Step 2: level interactions
     e = timed(P, "mac_level0", st, [&] {
         return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
                               P->near_kernel, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "near-field products");
-    for (int l = 1; l <= P->Lmac; ++l) {
-        DevLevel& D = lev[size_t(l)];
-        if (!D.m2l) continue;
-        e = timed(P, l == 1 ? "mac_interval_l1" : "mac_interval_l2plus", st, [&] {
-            return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, P->interval_kernel, st);
-        });
-        if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
-    }
-    // Step 3: downward pass
-    for (int l = P->Lmac; l >= 1; --l) {
-        DevLevel& D = lev[size_t(l)];
+    // ---- level 1 on s1: forward FFT, products, inverse FFT into u~1
+    if (Lm >= 1) {
+        DevLevel& D = lev[1];
         if (D.m2l) {
-            e = timed(P, "c2r_interval", st, [&] {
-                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, st);
+            e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
+            if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
+            e = timed(P, "mac_interval_l1", s1, [&] {
+                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel, s1);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
+            e = timed(P, "c2r_interval", s1, [&] {
+                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s1);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
         } else {
-            e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), st);
+            e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), s1);
             if (e != cudaSuccess) return cuda_fail(e, "clear level field");
         }
-        if (l < P->Lmac) {
-            e = timed(P, "interp", st, [&] {
-                return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                                  static_cast<const T*>(lev[size_t(l) + 1].ut), W, st);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "interpolation");
-        }
+        LGF_CUDA(cudaEventRecord(P->join[0], s1));
     }
-    const T* add = P->Lmac >= 1 ? static_cast<const T*>(lev[1].ut) : nullptr;
+    // ---- levels >= 2 on s2: Reg + forward FFTs upward, products, then inverse
+    // FFTs and interpolation downward to level 2
+    if (Lm >= 2) {
+        for (int l = 2; l <= Lm; ++l) {
+            DevLevel& D = lev[size_t(l)];
+            const bool from_blocks = l == 2;
+            e = timed(P, "reg", s2, [&] {
+                return Lc::reg(nb, P->n_max, from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft),
+                               from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg, static_cast<T*>(D.ft), W, s2);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "regularization");
+            if (D.m2l) {
+                e = timed(P, "r2c_interval", s2, [&] {
+                    return Lc::r2c(P->SI, nI, static_cast<const T*>(D.ft), n3, D.r2c, D.n_r2c, D.fh, s2);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
+            }
+        }
+        for (int l = 2; l <= Lm; ++l) {
+            DevLevel& D = lev[size_t(l)];
+            if (!D.m2l) continue;
+            e = timed(P, "mac_interval_l2plus", s2, [&] {
+                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel, s2);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
+        }
+        for (int l = Lm; l >= 2; --l) {
+            DevLevel& D = lev[size_t(l)];
+            if (D.m2l) {
+                e = timed(P, "c2r_interval", s2, [&] {
+                    return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s2);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
+            } else {
+                e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), s2);
+                if (e != cudaSuccess) return cuda_fail(e, "clear level field");
+            }
+            if (l < Lm) {
+                e = timed(P, "interp", s2, [&] {
+                    return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
+                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, s2);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+            }
+        }
+        LGF_CUDA(cudaEventRecord(P->join[1], s2));
+    }
+    // ---- join, interpolate level 2 into level 1, and the level-0 output
+    if (Lm >= 1) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
+    if (Lm >= 2) {
+        LGF_CUDA(cudaStreamWaitEvent(st, P->join[1], 0));
+        DevLevel& D = lev[1];
+        e = timed(P, "interp", st, [&] {
+            return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
+                              static_cast<const T*>(lev[2].ut), W, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+    }
+    const T* add = Lm >= 1 ? static_cast<const T*>(lev[1].ut) : nullptr;
     e = timed(P, "c2r_level0", st, [&] {
         return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
     });
@@ -731,6 +789,9 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
     if (s != LGF_OK) return s;
     s = build_plan(P.get(), block_ijk);
     if (s != LGF_OK) return s;
+    for (auto& a : P->aux) LGF_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    LGF_CUDA(cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming));
+    for (auto& j : P->join) LGF_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
     *out = P.release();
     return ok();
 }
