@@ -285,6 +285,15 @@ def main():
         total_ms = float(t.item())
     value = world * npts * args.steps / (total_ms * 1e-3)
 
+    # the same kernels once more with every launch on one stream, so the
+    # dominant kernel is also timed without other chains sharing the SMs
+    s_iso = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, fft_size_interval=args.fft_size,
+                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel, single_stream=1)
+    k_iso = max(3, min(100, args.steps // 10))
+    timed_steps(s_iso, f32, u32, k_iso, 3, timing_capacity=k_iso * 16)
+    kt_iso, _ = lgfm.lgf_plan_timings(s_iso.plan)
+    s_iso.close()
+
     # FP64 form on the same GPU (shorter run)
     s64, f64, u64 = make(lgfm.LGF_FP64)
     k64 = max(3, min(50, args.steps // 20))
@@ -318,10 +327,13 @@ def main():
         flops = 8.0 * pairs[lvl] * nw[lvl]                 # one complex MAC = 8 real flops
         peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
         ach = flops / (dom_ms * 1e-3) / 1e12
+        iso_ms = kt_iso[dom_name][0] / kt_iso[dom_name][1]
         roof = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
-                "algorithmic": f"8 flop x {pairs[lvl]} interaction pairs x {nw[lvl]} frequencies"}
+                "algorithmic": f"8 flop x {pairs[lvl]} interaction pairs x {nw[lvl]} frequencies",
+                "ms_in_step": dom_ms, "ms_isolated": iso_ms,
+                "frac_isolated": flops / (iso_ms * 1e-3) / 1e12 / peak_tf}
     else:
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": None, "peak": pk.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}
@@ -341,6 +353,7 @@ def main():
         "gpu_launches": int(per_solve_launches) * args.steps,
         "launches_per_step": int(per_solve_launches),
         "kernel_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
+        "kernel_ms_isolated": {k: v[0] / v[1] for k, v in kt_iso.items()},
         "roofline": roof, "peaks": src,
         "clocks": clk, "wall_s_timed": wall,
     }

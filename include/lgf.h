@@ -99,14 +99,19 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      frequency per thread, 2 = two frequencies per thread,
  *                      3 = two sibling groups per warp sharing coefficient
  *                      loads (2 and 3: FP32 only; FP64 plans use 1)
- * All variants compute the same sums (Eq. alg_mult) in the same order per
- * target; they differ only in scheduling.
+ *   single_stream      1 = run every kernel of a solve on the caller's stream;
+ *                      0 (default) = the level-1 chain and the levels >= 2
+ *                      chain run on two plan-owned streams forked from and
+ *                      joined into the caller's stream
+ * All variants compute the same sums (Eq. alg_mult); they differ only in
+ * scheduling.
  */
 typedef struct {
     int32_t fft_size_interval;
     int32_t near_kernel;
     int32_t interval_kernel;
-    int32_t reserved[13];
+    int32_t single_stream;
+    int32_t reserved[12];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */

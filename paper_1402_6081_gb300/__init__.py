@@ -107,7 +107,8 @@ MAX_LEVELS = 24
 
 class lgf_plan_options(ctypes.Structure):
     _fields_ = [("fft_size_interval", ctypes.c_int32), ("near_kernel", ctypes.c_int32),
-                ("interval_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 13)]
+                ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 12)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -133,13 +134,15 @@ def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
 
 def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
-                       fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0) -> int:
+                       fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
+                       single_stream: int = 0) -> int:
     """lgf_plan_create with tuning options (0 = default)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
     opts = lgf_plan_options()
     opts.fft_size_interval = fft_size_interval
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
+    opts.single_stream = single_stream
     out = ctypes.c_void_p()
     _check(library().lgf_plan_create_ex(b.ctypes.data, len(b), n_b, n_levels, interp_order, precision,
                                         interp_mode, ctypes.byref(opts), ctypes.byref(out)),
@@ -252,13 +255,14 @@ class Solver:
     with f, u torch CUDA tensors of shape (n_blocks, n_b, n_b, n_b)."""
 
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
-                 fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0):
+                 fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
+                 single_stream: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
         self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision,
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
-                                       interval_kernel=interval_kernel)
+                                       interval_kernel=interval_kernel, single_stream=single_stream)
 
     @property
     def dtype(self):

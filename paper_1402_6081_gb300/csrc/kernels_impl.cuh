@@ -41,7 +41,24 @@ constexpr int kFftThreads = 256;
 // transformed cube with an odd row pitch, plus the staged real cube.
 template <typename T, int S, int N>
 __host__ __device__ constexpr size_t fft_smem_bytes() {
-    return sizeof(cx<T>) * size_t(N) * S * ((S / 2 + 1) | 1) + sizeof(T) * size_t(N) * N * (N | 1);
+    return sizeof(cx<T>) * size_t(N) * ((S * ((S / 2 + 1) | 1)) | 1) + sizeof(T) * size_t(N) * N * (N | 1);
+}
+
+// copy n reals (n % 4 == 0) with 16-byte vectors when both ends are aligned
+template <typename T, typename F>
+__device__ __forceinline__ void staged_copy(int n, const T* src, F&& put) {
+    if (sizeof(T) == 4 && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        for (int i = threadIdx.x; i < n / 4; i += blockDim.x) {
+            const float4 v = __ldg(s4 + i);
+            put(4 * i, T(v.x));
+            put(4 * i + 1, T(v.y));
+            put(4 * i + 2, T(v.z));
+            put(4 * i + 3, T(v.w));
+        }
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) put(i, __ldg(src + i));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -55,16 +72,16 @@ template <typename T, int S, int NIN>
 __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, int64_t src_stride,
                                                      const R2CItem* __restrict__ items,
                                                      cx<T>* __restrict__ spec) {
-    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NIN | 1;
+    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NIN | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
-    T* X = reinterpret_cast<T*>(B + NIN * S * NXP);
+    T* X = reinterpret_cast<T*>(B + NIN * PP);
     const R2CItem it = items[blockIdx.x];
     const T* in = src + int64_t(it.src) * src_stride;
     cx<T>* out = spec + int64_t(it.dst) * NWS;
 
-    for (int i = threadIdx.x; i < NIN * NIN * NIN; i += blockDim.x) X[(i / NIN) * RS + i % NIN] = in[i];
+    staged_copy<T>(NIN * NIN * NIN, in, [&](int i, T v) { X[(i / NIN) * RS + i % NIN] = v; });
     __syncthreads();
     // x pass: lines l and l + NP (rows of the (y, z) plane) as one complex transform
     constexpr int NL = NIN * NIN, NP = (NL + 1) / 2;
@@ -79,8 +96,8 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
             z[x] = x < NIN ? cx<T>{r0[x], has1 ? r1[x] : T(0)} : czero<T>();
         fft<S, S, -1, NIN>(z);
         const int y0 = l0 % NIN, z0 = l0 / NIN, y1 = l1 % NIN, z1 = l1 / NIN;
-        cx<T>* d0 = B + (z0 * S + y0) * NXP;
-        cx<T>* d1 = B + (z1 * S + y1) * NXP;
+        cx<T>* d0 = B + z0 * PP + y0 * NXP;
+        cx<T>* d1 = B + z1 * PP + y1 * NXP;
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
             const cx<T> a = z[k], b = z[(S - k) % S];
@@ -92,7 +109,7 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
     // y pass: lines (kx, z), in place within the column
     for (int l = threadIdx.x; l < NX * NIN; l += blockDim.x) {
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * S * NXP + kx;
+        cx<T>* col = B + zz * PP + kx;
         cx<T> v[S];
 #pragma unroll
         for (int y = 0; y < S; ++y) v[y] = y < NIN ? col[y * NXP] : czero<T>();
@@ -107,7 +124,7 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
         const cx<T>* col = B + ky * NXP + kx;
         cx<T> v[S];
 #pragma unroll
-        for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * S * NXP] : czero<T>();
+        for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * PP] : czero<T>();
         fft<S, S, -1, NIN>(v);
 #pragma unroll
         for (int kz = 0; kz < S; ++kz) out[int64_t(kz) * S * NX + l] = v[kz];
@@ -127,11 +144,11 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
                                                      T* __restrict__ dst, int64_t dst_stride,
                                                      const T* __restrict__ add, int add_n,
                                                      int64_t add_stride) {
-    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NOUT | 1;
+    constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NOUT | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
-    T* O = reinterpret_cast<T*>(B + NOUT * S * NXP);
+    T* O = reinterpret_cast<T*>(B + NOUT * PP);
     const C2RItem it = items[blockIdx.x];
     const cx<T>* in = spec + int64_t(it.src) * NWS;
 
@@ -144,13 +161,13 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
         fft<S, S, 1, S>(v);
         cx<T>* col = B + ky * NXP + kx;
 #pragma unroll
-        for (int zz = 0; zz < NOUT; ++zz) col[zz * S * NXP] = v[zz];
+        for (int zz = 0; zz < NOUT; ++zz) col[zz * PP] = v[zz];
     }
     __syncthreads();
     // y pass: lines (kx, z < NOUT); keep y < NOUT
     for (int l = threadIdx.x; l < NX * NOUT; l += blockDim.x) {
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * S * NXP + kx;
+        cx<T>* col = B + zz * PP + kx;
         cx<T> v[S];
 #pragma unroll
         for (int y = 0; y < S; ++y) v[y] = col[y * NXP];
@@ -165,8 +182,8 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
         const int l0 = p, l1 = p + NP;
         const bool has1 = l1 < NL;
         const int y0 = l0 % NOUT, z0 = l0 / NOUT, y1 = l1 % NOUT, z1 = l1 / NOUT;
-        const cx<T>* a = B + (z0 * S + y0) * NXP;
-        const cx<T>* b = B + ((has1 ? z1 : z0) * S + (has1 ? y1 : y0)) * NXP;
+        const cx<T>* a = B + z0 * PP + y0 * NXP;
+        const cx<T>* b = B + (has1 ? z1 : z0) * PP + (has1 ? y1 : y0) * NXP;
         cx<T> z[S];
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
@@ -188,11 +205,27 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
     __syncthreads();
     T* out = dst + int64_t(it.dst) * dst_stride;
     const T* ad = (add != nullptr && it.aux >= 0) ? add + int64_t(it.aux) * add_stride : nullptr;
-    for (int i = threadIdx.x; i < NOUT * NOUT * NOUT; i += blockDim.x) {
-        const int x = i % NOUT, yz = i / NOUT;
-        T v = O[yz * RS + x];
-        if (ad) v += ad[((yz / NOUT) * add_n + yz % NOUT) * add_n + x];
-        out[i] = v;
+    constexpr int N3 = NOUT * NOUT * NOUT;
+    if (sizeof(T) == 4 && NOUT % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        for (int i = threadIdx.x; i < N3 / 4; i += blockDim.x) {
+            const int x = (4 * i) % NOUT, yz = (4 * i) / NOUT;
+            T v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = O[yz * RS + x + j];
+            if (ad) {
+                const T* a = ad + ((yz / NOUT) * add_n + yz % NOUT) * add_n + x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] += a[j];
+            }
+            reinterpret_cast<float4*>(out)[i] = make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3]));
+        }
+    } else {
+        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+            const int x = i % NOUT, yz = i / NOUT;
+            T v = O[yz * RS + x];
+            if (ad) v += ad[((yz / NOUT) * add_n + yz % NOUT) * add_n + x];
+            out[i] = v;
+        }
     }
 }
 

@@ -278,6 +278,7 @@ struct lgf_plan_s {
     int64_t n_blocks = 0, n_points = 0;
     int S0 = 0, SI = 0, Lmac = 0;
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
+    int single_stream = 0;
     std::vector<lgf::DevLevel> lev;
     std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
     void* W = nullptr;                  // device copy (unused by the kernels, kept for tools)
@@ -611,9 +612,10 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     else W = reinterpret_cast<const T*>(P->Wf.data());
     cudaError_t e;
     const int Lm = P->Lmac;
-    cudaStream_t s1 = P->aux[0], s2 = P->aux[1];
+    const bool conc = !P->single_stream;
+    cudaStream_t s1 = conc ? P->aux[0] : st, s2 = conc ? P->aux[1] : st;
     // fork: the other chains start after all prior work on the caller's stream
-    if (Lm >= 1) {
+    if (conc && Lm >= 1) {
         LGF_CUDA(cudaEventRecord(P->fork, st));
         LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
         if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
@@ -644,7 +646,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), s1);
             if (e != cudaSuccess) return cuda_fail(e, "clear level field");
         }
-        LGF_CUDA(cudaEventRecord(P->join[0], s1));
+        if (conc) LGF_CUDA(cudaEventRecord(P->join[0], s1));
     }
     // ---- levels >= 2 on s2: Reg + forward FFTs upward, products, then inverse
     // FFTs and interpolation downward to level 2
@@ -691,12 +693,12 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                 if (e != cudaSuccess) return cuda_fail(e, "interpolation");
             }
         }
-        LGF_CUDA(cudaEventRecord(P->join[1], s2));
+        if (conc) LGF_CUDA(cudaEventRecord(P->join[1], s2));
     }
     // ---- join, interpolate level 2 into level 1, and the level-0 output
-    if (Lm >= 1) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
+    if (conc && Lm >= 1) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
     if (Lm >= 2) {
-        LGF_CUDA(cudaStreamWaitEvent(st, P->join[1], 0));
+        if (conc) LGF_CUDA(cudaStreamWaitEvent(st, P->join[1], 0));
         DevLevel& D = lev[1];
         e = timed(P, "interp", st, [&] {
             return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
@@ -784,6 +786,7 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
             return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..3");
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
+        P->single_stream = opts->single_stream != 0;
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;

@@ -200,6 +200,19 @@ def test_deterministic_and_host_and_batch_paths():
     s2.close()
 
 
+def test_single_stream_matches_concurrent_chains():
+    # same kernels, same arithmetic: identical bits whichever streams run them
+    p = W.config(1)
+    f = torch.from_numpy(p.f).float().cuda()
+    a = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    b = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, single_stream=1)
+    ua, ub = a(f), b(f)
+    torch.cuda.synchronize()
+    assert torch.equal(ua, ub)
+    a.close()
+    b.close()
+
+
 def test_timing_api_counts_launches():
     p = W.config(1)
     s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
