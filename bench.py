@@ -106,6 +106,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel sources changed after that capture."""
+    import hashlib
+    if name != "mac_interval_l1":
+        return None
+    path = os.path.join(ROOT, "profiles", "mac_interval_torus_box_128_fp32.md")
+    csrc = os.path.join(ROOT, "paper_1402_6081_gb300", "csrc")
+    try:
+        text = open(path).read()
+        h = hashlib.sha256(open(os.path.join(csrc, "kernels_impl.cuh"), "rb").read()
+                           + open(os.path.join(csrc, "fft_device.cuh"), "rb").read()).hexdigest()[:16]
+        kv = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and "_" in line.split(": ")[0]
+                  and " " not in line.split(": ")[0])
+        if kv.get("kernel_source_sha256_16") != h:
+            return None
+        return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def interaction_pairs(blocks: np.ndarray, n_levels: int):
     """Source-target interval pairs per level: level 0 near pairs, level l >= 1
     interaction-list pairs (Sec. 3.1 lists), for the roofline's work count."""
@@ -329,7 +350,7 @@ def main():
         ach = flops / (dom_ms * 1e-3) / 1e12
         iso_ms = kt_iso[dom_name][0] / kt_iso[dom_name][1]
         roof = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": None,
+                "frac": ach / peak_tf, "traffic": profiled_traffic(dom_name),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
                 "algorithmic": f"8 flop x {pairs[lvl]} interaction pairs x {nw[lvl]} frequencies",
                 "ms_in_step": dom_ms, "ms_isolated": iso_ms,

@@ -23,6 +23,7 @@ import paper_1402_6081_gb300 as lgfm
 import workloads as W
 from oracle import direct, fmm
 from paper_1402_6081_gb300 import build as lgf_build
+from conftest import record_error
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +72,7 @@ def check(p, tol64=TOL64, tol32=TOL32):
     k = kappa(p)
     e64 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ref)
     e32 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ref)
+    record_error(p.name, fp64_vs_oracle=e64, fp32_vs_oracle=e32, kappa=k)
     assert e64 <= tol64 * k, ("fp64", e64, k)
     assert e32 <= tol32 * k, ("fp32", e32, k)
     return e64, e32
@@ -80,8 +82,11 @@ def test_gaussian_32_two_levels_vs_direct_sum():
     # 32^3 Gaussian, 4^3 blocks of 8^3, two levels, order 6: exact method
     p = W.config(0)
     ud = direct.direct_sum(p.blocks, p.n_b, p.f)
-    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ud) <= TOL64
-    assert fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ud) <= TOL32
+    e64 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ud)
+    e32 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ud)
+    record_error("gaussian_box_32 vs direct sum", fp64=e64, fp32=e32)
+    assert e64 <= TOL64
+    assert e32 <= TOL32
     check(p)
 
 
@@ -247,6 +252,7 @@ def test_irregular_512_fp32_vs_fp64(irregular):
     p = irregular
     u64 = gpu_solve(p, lgfm.LGF_FP64)
     u32 = gpu_solve(p, lgfm.LGF_FP32)
+    record_error("tori_irregular_512", fp32_vs_fp64=fmm.rel_linf(u32, u64))
     assert fmm.rel_linf(u32, u64) <= 2e-5          # kappa = 1 (non-negative source)
     assert np.all(np.isfinite(u64)) and np.abs(u64).max() > 0
 
@@ -264,4 +270,6 @@ def test_irregular_512_manufactured(irregular):
     u64 = gpu_solve(m, lgfm.LGF_FP64)
     assert fmm.rel_linf(u64, m.u_exact) < 1e-7
     u32 = gpu_solve(m, lgfm.LGF_FP32)
+    record_error("tori_irregular_512 manufactured", fp64_vs_exact=fmm.rel_linf(u64, m.u_exact),
+                 fp32_vs_exact=fmm.rel_linf(u32, m.u_exact))
     assert fmm.rel_linf(u32, u64) < 1e-5 * 5e3
