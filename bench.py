@@ -342,17 +342,21 @@ def main():
     assert pairs == interaction_pairs(p.blocks, p.n_levels)
     S0, SI = st["fft_size_level0"], st["fft_size_interval"]
     nw = {0: st["nw"][0], 1: st["nw"][1]}
+    # useful complex products per launch of each product kernel
+    work = {"mac_level0": (pairs[0] * nw[0], f"{pairs[0]} near pairs x {nw[0]} frequencies"),
+            "mac_level01": ((pairs[0] + pairs[1]) * nw[0],
+                            f"({pairs[0]} near + {pairs[1]} level-1 interaction pairs) x {nw[0]} frequencies"),
+            "mac_interval_l1": (pairs[1] * nw[1], f"{pairs[1]} interaction pairs x {nw[1]} frequencies")}
     roof = None
-    if dom_name.startswith("mac_"):
-        lvl = 0 if dom_name == "mac_level0" else 1
-        flops = 8.0 * pairs[lvl] * nw[lvl]                 # one complex MAC = 8 real flops
+    if dom_name in work:
+        flops = 8.0 * work[dom_name][0]                   # one complex MAC = 8 real flops
         peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
         ach = flops / (dom_ms * 1e-3) / 1e12
         iso_ms = kt_iso[dom_name][0] / kt_iso[dom_name][1]
         roof = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": profiled_traffic(dom_name),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
-                "algorithmic": f"8 flop x {pairs[lvl]} interaction pairs x {nw[lvl]} frequencies",
+                "algorithmic": "8 flop x " + work[dom_name][1],
                 "ms_in_step": dom_ms, "ms_isolated": iso_ms,
                 "frac_isolated": flops / (iso_ms * 1e-3) / 1e12 / peak_tf}
     else:

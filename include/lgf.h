@@ -103,6 +103,16 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      0 (default) = the level-1 chain and the levels >= 2
  *                      chain run on two plan-owned streams forked from and
  *                      joined into the caller's stream
+ *   separate_level1    0 (default): the level-1 interaction list is summed
+ *                      into the level-0 spectra.  Level-1 nodes are the grid
+ *                      points and only the first n_b nodes of a level-1
+ *                      interval are used (Sec. 4), so the level-0 transform
+ *                      length 2 n_b already gives the exact level-1
+ *                      convolution; by linearity both levels then share one
+ *                      forward FFT, one product pass over the 6^3 blocks of
+ *                      the parent neighbourhood (343 kernel offsets) and one
+ *                      inverse FFT.  1: separate level-1 transforms of length
+ *                      S_I, as the level interactions of Sec. 3.1 are listed.
  * All variants compute the same sums (Eq. alg_mult); they differ only in
  * scheduling.
  */
@@ -111,7 +121,8 @@ typedef struct {
     int32_t near_kernel;
     int32_t interval_kernel;
     int32_t single_stream;
-    int32_t reserved[12];
+    int32_t separate_level1;
+    int32_t reserved[11];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */
@@ -126,6 +137,8 @@ lgf_status lgf_plan_create_ex(const int32_t *block_ijk, int64_t n_blocks, int32_
  *   intervals[l], groups[l]   intervals and sibling groups per level
  *   nw[l]      frequencies per spectrum at level l (0 where l has no products)
  *   top_product_level  highest level with a non-empty interaction list
+ *   merged_level01     1 if levels 0 and 1 share one product pass (nw[1] is
+ *                      then the level-0 spectrum size)
  */
 #define LGF_MAX_LEVELS 24
 typedef struct {
@@ -136,6 +149,7 @@ typedef struct {
     int64_t groups[LGF_MAX_LEVELS + 1];
     int64_t nw[LGF_MAX_LEVELS + 1];
     int64_t workspace_bytes;
+    int32_t merged_level01;
 } lgf_plan_stats;
 
 lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);

@@ -108,7 +108,7 @@ MAX_LEVELS = 24
 class lgf_plan_options(ctypes.Structure):
     _fields_ = [("fft_size_interval", ctypes.c_int32), ("near_kernel", ctypes.c_int32),
                 ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 12)]
+                ("separate_level1", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -119,7 +119,7 @@ class lgf_plan_stats(ctypes.Structure):
                 ("intervals", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("groups", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32)]
 
 
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
@@ -135,7 +135,7 @@ def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
 def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
                        fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                       single_stream: int = 0) -> int:
+                       single_stream: int = 0, separate_level1: int = 0) -> int:
     """lgf_plan_create with tuning options (0 = default)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
     opts = lgf_plan_options()
@@ -143,6 +143,7 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
     opts.single_stream = single_stream
+    opts.separate_level1 = separate_level1
     out = ctypes.c_void_p()
     _check(library().lgf_plan_create_ex(b.ctypes.data, len(b), n_b, n_levels, interp_order, precision,
                                         interp_mode, ctypes.byref(opts), ctypes.byref(out)),
@@ -158,7 +159,8 @@ def lgf_plan_get_stats(plan: int) -> dict:
             "top_product_level": st.top_product_level, "fft_size_level0": st.fft_size_level0,
             "fft_size_interval": st.fft_size_interval, "pairs": list(st.pairs[: L + 1]),
             "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
-            "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes}
+            "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes,
+            "merged_level01": st.merged_level01}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:
@@ -256,13 +258,14 @@ class Solver:
 
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                 single_stream: int = 0):
+                 single_stream: int = 0, separate_level1: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
         self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision,
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
-                                       interval_kernel=interval_kernel, single_stream=single_stream)
+                                       interval_kernel=interval_kernel, single_stream=single_stream,
+                                       separate_level1=separate_level1)
 
     @property
     def dtype(self):

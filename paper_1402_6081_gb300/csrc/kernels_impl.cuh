@@ -296,14 +296,16 @@ struct MacWalk {
     int g, e;            // current pair (g: position in the work order; e < 0: no neighbours)
     int gid;             // group id at position g
     unsigned mask;       // neighbours of gid not yet visited
+    int self;            // whether the group's own block (e = 13) is a source
 };
 
-__device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g) {
+// present neighbour groups; the group itself (e = 13) only when include_self
+__device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g, int include_self = 0) {
     const int* nb = gnbr + int64_t(g) * 27;
     unsigned m = 0;
 #pragma unroll
     for (int e = 0; e < 27; ++e)
-        if (e != 13 && __ldg(nb + e) >= 0) m |= 1u << e;
+        if ((e != 13 || include_self) && __ldg(nb + e) >= 0) m |= 1u << e;
     return m;
 }
 
@@ -318,7 +320,7 @@ __device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gn
     it.g += kMacWarps;
     if (it.g >= g1) return false;
     it.gid = __ldg(order + it.g);
-    it.mask = nbr_mask(gnbr, it.gid);
+    it.mask = nbr_mask(gnbr, it.gid, it.self);
     if (it.mask) {
         it.e = __ffs(it.mask) - 1;
         it.mask &= it.mask - 1;
@@ -362,14 +364,16 @@ __device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], 
 }
 
 // Groups are visited in the plan's work order (sorted by neighbour count, so
-// the warps of one CTA carry similar work).
+// the warps of one CTA carry similar work).  With include_self the group's own
+// sibling block e = 13 is a source too: that is the merged level-0 / level-1
+// form, where the 343 coefficient rows hold the near offsets as well.
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_interval(const cx<T>* __restrict__ fh,
                                                                    const cx<T>* __restrict__ kh,
                                                                    cx<T>* __restrict__ uh,
                                                                    const int* __restrict__ gnbr,
                                                                    const int* __restrict__ order, int n_groups,
-                                                                   int groups_per_cta) {
+                                                                   int groups_per_cta, int include_self) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
-    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0, 0u};
+    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0, 0u, include_self};
     if (!mac_next(cur, gnbr, order, g1)) return;
     cx<T> Fa[8], Fb[8], acc[8];
 #pragma unroll
@@ -892,7 +896,8 @@ __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ chil
 template <typename T, int NI>
 __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__ slot,
                                                          const int* __restrict__ parent, T* __restrict__ u,
-                                                         const T* __restrict__ up, const InterpW<T, NI> W) {
+                                                         const T* __restrict__ up, const InterpW<T, NI> W,
+                                                         int accumulate) {
     constexpr int N2 = NI * NI, N3 = NI * NI * NI;
     __shared__ T a[N3];
     const int t = threadIdx.x;
@@ -930,8 +935,13 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
         for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
         apply_w(W, czp, in, out);
         T* o = u + int64_t(s) * N3 + t;
+        if (accumulate) {
 #pragma unroll
-        for (int z = 0; z < NI; ++z) o[z * N2] += out[z];
+            for (int z = 0; z < NI; ++z) o[z * N2] += out[z];
+        } else {
+#pragma unroll
+            for (int z = 0; z < NI; ++z) o[z * N2] = out[z];
+        }
     }
 }
 
@@ -1018,7 +1028,7 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
 
 template <typename T, int S>
 static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                       int n_groups, int variant, cudaStream_t st) {
+                                       int n_groups, int variant, int include_self, cudaStream_t st) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     const auto* f = static_cast<const dev::cx<T>*>(fh);
     const auto* k = static_cast<const dev::cx<T>*>(kh);
@@ -1031,6 +1041,7 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
             per *= 2;
         return per;
     };
+    if (include_self) variant = 1;
     if (variant == 3 && sizeof(T) == 4) {
         const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
         auto kern = dev::k_mac_interval_pair<T, S>;
@@ -1065,22 +1076,21 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
     const int64_t nchunks = (NW + 31) / 32;
     const int per = groups_per_cta(dev::kMacWarps, sizeof(T) == 4 ? 2 : 1, nchunks);
     dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
-    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per);
+    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                    int n_groups, int S, int variant, cudaStream_t st) {
+                                    int n_groups, int S, int variant, int include_self, cudaStream_t st) {
+#define LGF_MACI(SS) \
+    case SS: return launch_mac_interval<T, SS>(fh, kh, uh, gnbr, order, n_groups, variant, include_self, st);
     switch (S) {
-        case 10: return launch_mac_interval<T, 10>(fh, kh, uh, gnbr, order, n_groups, variant, st);
-        case 17: return launch_mac_interval<T, 17>(fh, kh, uh, gnbr, order, n_groups, variant, st);
-        case 18: return launch_mac_interval<T, 18>(fh, kh, uh, gnbr, order, n_groups, variant, st);
-        case 33: return launch_mac_interval<T, 33>(fh, kh, uh, gnbr, order, n_groups, variant, st);
-        case 34: return launch_mac_interval<T, 34>(fh, kh, uh, gnbr, order, n_groups, variant, st);
-        case 36: return launch_mac_interval<T, 36>(fh, kh, uh, gnbr, order, n_groups, variant, st);
+        LGF_MACI(8) LGF_MACI(10) LGF_MACI(16) LGF_MACI(17) LGF_MACI(18) LGF_MACI(32) LGF_MACI(33) LGF_MACI(34)
+        LGF_MACI(36)
         default: return cudaErrorInvalidValue;
     }
+#undef LGF_MACI
 }
 
 template <typename T, int NI>
@@ -1111,12 +1121,13 @@ cudaError_t Launch<T>::reg(int n_b, int /*n_max*/, const T* child_src, int child
 
 template <typename T>
 cudaError_t Launch<T>::interp(int n_b, const int* slot, const int* parent, int n_items, T* u,
-                              const T* up, const T* W, cudaStream_t st) {
+                              const T* up, const T* W, int accumulate, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-#define LGF_INTERP(NI)                                                                                   \
-    if (n_b + 1 == NI) {                                                                                 \
-        dev::k_interp<T, NI><<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W)); \
-        return cudaGetLastError();                                                                       \
+#define LGF_INTERP(NI)                                                                                      \
+    if (n_b + 1 == NI) {                                                                                    \
+        dev::k_interp<T, NI><<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W),    \
+                                                                   accumulate);                            \
+        return cudaGetLastError();                                                                          \
     }
     LGF_INTERP(5) LGF_INTERP(9) LGF_INTERP(17)
 #undef LGF_INTERP

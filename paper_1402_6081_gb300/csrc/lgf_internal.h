@@ -74,16 +74,17 @@ struct Launch {
     // variant: 0/2 default form, 1 the earlier form (kept for comparison)
     static cudaError_t mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr,
                                   int n_groups, int S, int variant, cudaStream_t st);
-    // order: the groups in work order (descending neighbour count)
+    // order: the groups in work order (descending neighbour count);
+    // include_self: the group's own block is a source (merged levels 0 and 1)
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                    int n_groups, int S, int variant, cudaStream_t st);
+                                    int n_groups, int S, int variant, int include_self, cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,
                            const int* child_index, const int* parent_slot, int n_parents,
                            T* dst, const T* W, cudaStream_t st);
-    // u[slot] += Interp(u_parent[parent]) for each item.
+    // u[slot] (+)= Interp(u_parent[parent]) for each item (accumulate: add, else store).
     static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items,
-                              T* u, const T* up, const T* W, cudaStream_t st);
+                              T* u, const T* up, const T* W, int accumulate, cudaStream_t st);
 };
 
 }  // namespace lgf

@@ -150,9 +150,14 @@ void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double*
 static std::mutex g_spec_mu;
 static std::map<SpecKey, std::weak_ptr<SpecEntry>> g_spec_cache;
 
-static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int prec,
+// kind: kNear (27 offsets |d| <= 1, n = n_b), kInterval (343 offsets |d| <= 3,
+// n = n_I, zero at the near ones), kBlock (343 offsets |d| <= 3, n = n_b, all
+// filled: level 0 near field and level-1 interaction list on the block grid)
+enum SpecKind { kNear = 0, kInterval = 1, kBlock = 2 };
+
+static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int prec,
                               std::shared_ptr<SpecEntry>& out) {
-    const SpecKey key{device, n_b, S, h, near ? 1 : 0, prec};
+    const SpecKey key{device, n_b, S, h, kind, prec};
     std::lock_guard<std::mutex> lock(g_spec_mu);
     auto it = g_spec_cache.find(key);
     if (it != g_spec_cache.end()) {
@@ -161,8 +166,9 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int 
             return ok();
         }
     }
-    const int n = near ? n_b : n_b + 1;
-    const int V = near ? 2 * n_b - 1 : 4 * n_b;
+    const bool near = kind == kNear;
+    const int n = kind == kInterval ? n_b + 1 : n_b;
+    const int V = near ? 2 * n_b - 1 : kind == kBlock ? 4 * n_b - 1 : 4 * n_b;
     auto tab = green_abs_table(h, V);
     const int nd = near ? 27 : 343;
     const int64_t NW = nw_of(S), NWS = nws_of(S);
@@ -172,7 +178,7 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, bool near, int 
         const int r = near ? 3 : 7, o = near ? 1 : 3;
         const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
         const bool is_near = std::abs(d[0]) <= 1 && std::abs(d[1]) <= 1 && std::abs(d[2]) <= 1;
-        if (near || !is_near) todo.push_back(id);
+        if (kind != kInterval || !is_near) todo.push_back(id);
     }
     unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
@@ -279,6 +285,10 @@ struct lgf_plan_s {
     int S0 = 0, SI = 0, Lmac = 0;
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     int single_stream = 0;
+    // levels 0 and 1 share the block grid and S0 = 2 n_b suffices for the
+    // first n_b nodes of a level-1 interval: their products are summed into
+    // one spectrum per block (one inverse FFT, no level-1 transforms)
+    bool merged = true;
     std::vector<lgf::DevLevel> lev;
     std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
     void* W = nullptr;                  // device copy (unused by the kernels, kept for tools)
@@ -475,7 +485,7 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         const auto& L_ = lv[size_t(l)];
         DevLevel& D = P->lev[size_t(l)];
         D.n_groups = int(L_.groups.size());
-        D.m2l = (l == 0) || L_.m2l;
+        D.m2l = (l == 0) || (L_.m2l && !(l == 1 && P->merged));
         const size_t slots = size_t(D.n_groups) * 8;
         lgf_status s;
         if (D.m2l) {
@@ -509,9 +519,10 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
             D.n_r2c = int(items.size());
             if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
             const int h = l == 0 ? 1 : (1 << (l - 1));
-            if ((s = get_spectra(P->device, nb, S, h, l == 0, P->prec, D.kh)) != LGF_OK) return s;
+            const int kind = l == 0 ? (P->merged ? kBlock : kNear) : kInterval;
+            if ((s = get_spectra(P->device, nb, S, h, kind, P->prec, D.kh)) != LGF_OK) return s;
         }
-        if (l >= 1) {
+        if (l >= 1 && !(l == 1 && P->merged && Lmac < 2)) {
             if ((s = dalloc(P, slots * n3 * elem, &D.ut, true)) != LGF_OK) return s;
             if (D.m2l) {
                 std::vector<C2RItem> items;
@@ -558,7 +569,8 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         std::vector<C2RItem> items;
         for (int64_t b = 0; b < NB; ++b) {
             const int slot = lv[0].slot(blocks[size_t(b)]);
-            items.push_back({slot, int(b), Lmac >= 1 ? slot : -1});
+            const bool has_ut1 = P->merged ? Lmac >= 2 : Lmac >= 1;
+            items.push_back({slot, int(b), has_ut1 ? slot : -1});
         }
         P->n_out = int(items.size());
         lgf_status s = upload(P, items, &P->out_items);
@@ -615,27 +627,36 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     const bool conc = !P->single_stream;
     cudaStream_t s1 = conc ? P->aux[0] : st, s2 = conc ? P->aux[1] : st;
     // fork: the other chains start after all prior work on the caller's stream
-    if (conc && Lm >= 1) {
+    if (conc && (Lm >= 2 || (Lm >= 1 && !P->merged))) {
         LGF_CUDA(cudaEventRecord(P->fork, st));
-        LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
+        if (!P->merged) LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
         if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
     }
     // ---- level 0 on the caller's stream: forward FFT, near-field products
     e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
     if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
-    e = timed(P, "mac_level0", st, [&] {
-        return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
-                              P->near_kernel, st);
-    });
+    if (P->merged) {
+        e = timed(P, "mac_level01", st, [&] {
+            return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
+                                    P->S0, 1, 1, st);
+        });
+    } else {
+        e = timed(P, "mac_level0", st, [&] {
+            return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
+                                  P->near_kernel, st);
+        });
+    }
     if (e != cudaSuccess) return cuda_fail(e, "near-field products");
-    // ---- level 1 on s1: forward FFT, products, inverse FFT into u~1
-    if (Lm >= 1) {
+    // ---- level 1 on s1: forward FFT, products, inverse FFT into u~1 (merged
+    // form: already part of the level-0 products)
+    if (Lm >= 1 && !P->merged) {
         DevLevel& D = lev[1];
         if (D.m2l) {
             e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
             if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
             e = timed(P, "mac_interval_l1", s1, [&] {
-                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel, s1);
+                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
+                                        0, s1);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
             e = timed(P, "c2r_interval", s1, [&] {
@@ -670,7 +691,8 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             DevLevel& D = lev[size_t(l)];
             if (!D.m2l) continue;
             e = timed(P, "mac_interval_l2plus", s2, [&] {
-                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel, s2);
+                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
+                                        0, s2);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
         }
@@ -688,7 +710,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             if (l < Lm) {
                 e = timed(P, "interp", s2, [&] {
                     return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, s2);
+                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, 1, s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interpolation");
             }
@@ -696,17 +718,20 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if (conc) LGF_CUDA(cudaEventRecord(P->join[1], s2));
     }
     // ---- join, interpolate level 2 into level 1, and the level-0 output
-    if (conc && Lm >= 1) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
+    if (conc && Lm >= 1 && !P->merged) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
     if (Lm >= 2) {
         if (conc) LGF_CUDA(cudaStreamWaitEvent(st, P->join[1], 0));
         DevLevel& D = lev[1];
+        // merged form: u~1 holds only the interpolated level-2 field (stored);
+        // otherwise it already holds the level-1 products' field (added to)
         e = timed(P, "interp", st, [&] {
             return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                              static_cast<const T*>(lev[2].ut), W, st);
+                              static_cast<const T*>(lev[2].ut), W, P->merged ? 0 : 1, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interpolation");
     }
-    const T* add = Lm >= 1 ? static_cast<const T*>(lev[1].ut) : nullptr;
+    const bool has_ut1 = P->merged ? Lm >= 2 : Lm >= 1;
+    const T* add = has_ut1 ? static_cast<const T*>(lev[1].ut) : nullptr;
     e = timed(P, "c2r_level0", st, [&] {
         return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
     });
@@ -787,6 +812,7 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
         P->single_stream = opts->single_stream != 0;
+        P->merged = opts->separate_level1 == 0;
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
@@ -823,6 +849,8 @@ lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
         st->groups[l] = plan->groups[size_t(l)];
         if (l <= plan->Lmac && plan->lev[size_t(l)].m2l) st->nw[l] = nw_of(l == 0 ? plan->S0 : plan->SI);
     }
+    st->merged_level01 = plan->merged ? 1 : 0;
+    if (plan->merged && plan->Lmac >= 1) st->nw[1] = nw_of(plan->S0);
     size_t b = 0;
     lgf_plan_workspace_bytes(plan, &b);
     st->workspace_bytes = int64_t(b);

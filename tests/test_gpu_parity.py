@@ -147,8 +147,9 @@ _variant_problem = None
 
 
 @pytest.mark.parametrize("S", [33, 34, 36])
-@pytest.mark.parametrize("near,interval", [(1, 1), (2, 2), (2, 1), (1, 2), (2, 3)])
-def test_kernel_variants_and_fft_lengths(S, near, interval):
+@pytest.mark.parametrize("near,interval,separate", [(1, 1, 1), (2, 2, 1), (2, 1, 1), (1, 2, 1), (2, 3, 1),
+                                                    (0, 0, 0), (0, 3, 0)])
+def test_kernel_variants_and_fft_lengths(S, near, interval, separate):
     # every product-kernel variant and interval FFT length computes the same
     # method (6^3 blocks of 16^3, 3 levels: level 2 has an interaction list)
     global _variant_problem
@@ -159,7 +160,7 @@ def test_kernel_variants_and_fft_lengths(S, near, interval):
     for prec, tol in ((lgfm.LGF_FP64, TOL64), (lgfm.LGF_FP32, TOL32)):
         dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
         s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=S,
-                        near_kernel=near, interval_kernel=interval)
+                        near_kernel=near, interval_kernel=interval, separate_level1=separate)
         u = s(torch.from_numpy(p.f).to(dt).cuda())
         torch.cuda.synchronize()
         err = fmm.rel_linf(u.double().cpu().numpy(), ref)
@@ -226,10 +227,18 @@ def test_timing_api_counts_launches():
     s(f)
     s(f)
     t, per = lgfm.lgf_plan_timings(s.plan)
-    # 128^3, 3 levels: r2c x3, reg, mac x3, c2r x3, interp
-    assert per == 11
-    assert t["mac_interval_l1"][1] == 2 and t["mac_interval_l1"][0] > 0
-    assert sum(c for _, c in t.values()) == 22
+    # 128^3, 3 levels, levels 0 and 1 merged: r2c x2, products x2, reg, c2r x2, interp
+    assert s.stats()["merged_level01"] == 1
+    assert per == 8
+    assert t["mac_level01"][1] == 2 and t["mac_level01"][0] > 0
+    assert sum(c for _, c in t.values()) == 16
+    s.close()
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, separate_level1=1)
+    lgfm.lgf_plan_set_timing(s.plan, 64)
+    s(f)
+    t, per = lgfm.lgf_plan_timings(s.plan)
+    # separate level 1: r2c x3, reg, products x3, c2r x3, interp
+    assert per == 11 and t["mac_interval_l1"][1] == 1
     s.close()
 
 
