@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T
 // loaded once and applied to A's and B's source blocks (each only if that
 // group has neighbour e, a warp-uniform test), which halves coefficient
 // traffic per product.  One CTA of kMacPWarps warps per SM (FP32 registers).
-constexpr int kMacPWarps = 8;
+constexpr int kMacPWarps = 16;
 
 template <typename T, int S>
 __device__ __forceinline__ void macp_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh, int q, int64_t wc) {
@@ -675,28 +675,33 @@ __device__ __forceinline__ void macp_load(cx<T> (&F)[8], const cx<T>* __restrict
     for (int c = 0; c < 8; ++c) F[c] = ldg_cx(src + c * NWS);
 }
 
+// Products of one neighbour offset e for groups A and B (each if present),
+// the 27 coefficients read in three slices of fixed dz = cs_z - ct_z so that
+// only 9 are live at a time.
 template <typename T>
-__device__ __forceinline__ void macp_coef(cx<T> (&kk)[27], const cx<T>* __restrict__ sk, int e) {
+__device__ __forceinline__ void macp_pair_block(cx<T> (&accA)[8], const cx<T> (&FA)[8], bool hasA,
+                                                cx<T> (&accB)[8], const cx<T> (&FB)[8], bool hasB,
+                                                const cx<T>* __restrict__ sk, int e) {
     const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
     const cx<T>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 32 + threadIdx.x;
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
+    for (int dz = -1; dz <= 1; ++dz) {
+        cx<T> kk[9];
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx)
-                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
-}
-
-template <typename T>
-__device__ __forceinline__ void macp_block(cx<T> (&acc)[8], const cx<T> (&F)[8], const cx<T> (&kk)[27]) {
+            for (int dx = -1; dx <= 1; ++dx) kk[(dx + 1) + 3 * (dy + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
 #pragma unroll
-    for (int ct = 0; ct < 8; ++ct)
+        for (int ct = 0; ct < 8; ++ct)
 #pragma unroll
-        for (int cs = 0; cs < 8; ++cs) {
-            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
-            acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
-        }
+            for (int cs = 0; cs < 8; ++cs) {
+                if ((cs >> 2) - (ct >> 2) != dz) continue;
+                const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1);
+                const cx<T> kv = kk[(dx + 1) + 3 * (dy + 1)];
+                if (hasA) accA[ct] = cmac(accA[ct], FA[cs], kv);
+                if (hasB) accB[ct] = cmac(accB[ct], FB[cs], kv);
+            }
+    }
 }
 
 template <typename T, int S>
@@ -704,7 +709,9 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
                                                                          const cx<T>* __restrict__ kh,
                                                                          cx<T>* __restrict__ uh,
                                                                          const int* __restrict__ gnbr,
-                                                                         int n_groups, int groups_per_cta) {
+                                                                         const int* __restrict__ order,
+                                                                         int n_groups, int groups_per_cta,
+                                                                         int include_self) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -721,10 +728,11 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
     const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
-    for (int ga = g0 + 2 * int(threadIdx.y); ga < g1; ga += 2 * kMacPWarps) {
-        const int gb = ga + 1 < g1 ? ga + 1 : -1;
-        const unsigned ma = nbr_mask(gnbr, ga);
-        const unsigned mb = gb >= 0 ? nbr_mask(gnbr, gb) : 0u;
+    for (int pa = g0 + 2 * int(threadIdx.y); pa < g1; pa += 2 * kMacPWarps) {
+        const int ga = __ldg(order + pa);
+        const int gb = pa + 1 < g1 ? __ldg(order + pa + 1) : -1;
+        const unsigned ma = nbr_mask(gnbr, ga, include_self);
+        const unsigned mb = gb >= 0 ? nbr_mask(gnbr, gb, include_self) : 0u;
         unsigned mask = ma | mb;
         cx<T> accA[8], accB[8];
 #pragma unroll
@@ -744,10 +752,7 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
                 cx<T> NA[8], NB[8];
                 if (en >= 0 && ((ma >> en) & 1)) macp_load<T, S>(NA, fh, __ldg(gnbr + int64_t(ga) * 27 + en), wc);
                 if (en >= 0 && ((mb >> en) & 1)) macp_load<T, S>(NB, fh, __ldg(gnbr + int64_t(gb) * 27 + en), wc);
-                cx<T> kk[27];
-                macp_coef(kk, sk, e);
-                if ((ma >> e) & 1) macp_block(accA, FA, kk);
-                if ((mb >> e) & 1) macp_block(accB, FB, kk);
+                macp_pair_block(accA, FA, ((ma >> e) & 1) != 0, accB, FB, ((mb >> e) & 1) != 0, sk, e);
                 if (en < 0) break;
                 e = en;
 #pragma unroll
@@ -1041,7 +1046,7 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
             per *= 2;
         return per;
     };
-    if (include_self) variant = 1;
+    if (include_self && variant == 2) variant = 1;
     if (variant == 3 && sizeof(T) == 4) {
         const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
         auto kern = dev::k_mac_interval_pair<T, S>;
@@ -1051,7 +1056,7 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
         const int64_t nchunks = (NW + 31) / 32;
         int per = groups_per_cta(2 * dev::kMacPWarps, 1, nchunks);
         dim3 block(32, dev::kMacPWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
-        kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
+        kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self);
         return cudaGetLastError();
     }
     // two frequencies per thread need 343 x 64 coefficients in shared memory:

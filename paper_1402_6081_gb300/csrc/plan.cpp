@@ -638,7 +638,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     if (P->merged) {
         e = timed(P, "mac_level01", st, [&] {
             return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
-                                    P->S0, 1, 1, st);
+                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, st);
         });
     } else {
         e = timed(P, "mac_level0", st, [&] {
