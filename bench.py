@@ -202,6 +202,126 @@ def run_reference(args):
     }))
 
 
+def batch_run(torch, lgfm, steps: int, warmup: int, flush):
+    """64 independent uneven solves (log-uniform 32^3..192^3 boxes, 8^3 or 16^3
+    blocks, Gaussian-blob sources) as one CUDA-graph batch: one multi-problem
+    plan per block size (one launch per phase for all its problems), options
+    from the autotuner.  Returns the JSON object of the batched workload."""
+    from paper_1402_6081_gb300 import autotune
+    probs = W.batch_problems(64, seed=3)
+    specs = [(p.blocks, p.n_b, p.n_levels, p.order) for p in probs]
+    opts = {}
+    for n_b in sorted({p.n_b for p in probs}):
+        ps = [p for p in probs if p.n_b == n_b]
+        opts[n_b] = autotune.tune_multi([p.blocks for p in ps], n_b, [p.n_levels for p in ps], ps[0].order,
+                                        lgfm.LGF_FP32)
+    stream = torch.cuda.Stream()
+    res = {}
+    for prec in (lgfm.LGF_FP32, lgfm.LGF_FP64):
+        dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+        bs = lgfm.BatchSolver(specs, prec, use_graph=1, options=opts if prec == lgfm.LGF_FP32 else None)
+        bs.set_sources([torch.from_numpy(p.f).to(dt) for p in probs])
+        launches = sum(lgfm.lgf_plan_timings(pl)[1] for pl in bs.plans)
+        k = steps if prec == lgfm.LGF_FP32 else max(3, steps // 5)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                bs(stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                flush.fill_(1.0)
+                a.record(stream)
+                bs(stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        npts = bs.n_points()
+        r = {"value": npts / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms, "steps": k,
+             "gpu_launches_per_step": int(launches), "plans": len(bs.plans)}
+        if prec == lgfm.LGF_FP32:
+            # end to end: pinned host sources in, results out, every step
+            fh = [torch.cat([bs.f_view(i).reshape(-1).cpu() for i in range(len(probs)) if bs.where[i][0] == c])
+                  .pin_memory() for c in range(len(bs.plans))]
+            uh = [torch.empty_like(x).pin_memory() for x in fh]
+            ke = max(3, k // 4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                with torch.cuda.stream(stream):
+                    for c in range(len(bs.plans)):
+                        bs.f[c].copy_(fh[c], non_blocking=True)
+                    bs(stream)
+                    for c in range(len(bs.plans)):
+                        uh[c].copy_(bs.u[c], non_blocking=True)
+                stream.synchronize()
+            e2e = (time.perf_counter() - t0) / ke
+            nbytes = int(sum(x.numel() for x in fh) * 4)
+            r["e2e"] = {"value": npts / e2e, "unit": "points/s", "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": nbytes, "steps": ke}
+            r["options"] = {str(kk): v for kk, v in opts.items()}
+            u32 = [bs.u_view(i).double().cpu().numpy() for i in range(len(probs))]
+        else:
+            err = 0.0
+            for i in range(len(probs)):
+                u64 = bs.u_view(i).cpu().numpy()
+                err = max(err, float(np.abs(u32[i] - u64).max() / np.abs(u64).max()))
+            r["rel_err_fp32_vs_fp64_max"] = err
+        bs.close()
+        res["fp32" if prec == lgfm.LGF_FP32 else "fp64"] = r
+    out = dict(res["fp32"])
+    out["fp64"] = res["fp64"]
+    out["config"] = {"workload": "batch64", "problems": len(probs), "points": npts,
+                     "l2": "flushed: 256 MiB write before every timed step", "graph": True}
+    return out
+
+
+def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
+    """Poisson arrivals (200/s, seed 1) of torus solves with point counts
+    log-uniform in 2^12..2^24, admitted under a 120 GB HBM budget, FP32 form
+    and plain FP64 form, plus one 512^3 fully occupied solve in the stream and
+    alone.  Latency: arrival to the result copied back to host memory."""
+    from paper_1402_6081_gb300.serve import GpuServer, Request, summarize
+    arr = W.arrival_stream(n_requests, 200.0, seed=1)
+    shapes = sorted({(n_b, nb) for _, n_b, nb in arr})
+    problems = {k: W.request_problem(k[0], k[1], seed=i) for i, k in enumerate(shapes)}
+    big = ("full", 512)
+    problems[big] = W.torus_box(seed=7, nb=32, n_b=16, radius=0.3 * 512, sigma=0.06 * 512, noise=0.05, order=8)
+    reqs = [Request(i, t, (n_b, nb), problems[(n_b, nb)].n_points) for i, (t, n_b, nb) in enumerate(arr)]
+    t_big = arr[(n_warm + n_requests) // 2][0]
+    reqs.append(Request(n_requests, t_big, big, problems[big].n_points))
+    npts = {r.rid: r.n_points for r in reqs}
+    out = {}
+    for prec in (lgfm.LGF_FP32, lgfm.LGF_FP64):
+        name = "fp32" if prec == lgfm.LGF_FP32 else "fp64"
+        srv = GpuServer(prec, problems, budget_bytes=120e9, n_streams=16)
+        srv.warm(shapes + [big])
+        done, rejected = srv.run(reqs)
+        timed = [d for d in done if n_warm <= d.rid < n_requests]
+        s = summarize(timed, lambda rid: npts[rid])
+        bigd = [d for d in done if d.rid == n_requests]
+        s["big_512_in_stream_ms"] = 1e3 * bigd[0].latency if bigd else None
+        s["rejected"] = len(rejected)
+        s["plans_resident"] = sum(len(v) for v in srv.pools.slots.values())
+        s["hbm_used_gb"] = srv.pools.used / 1e9
+        # the same 512^3 request alone
+        alone, _ = srv.run([Request(0, 0.0, big, problems[big].n_points)])
+        s["big_512_alone_ms"] = 1e3 * alone[0].latency
+        # saturated: every timed request present at once (capacity); the
+        # second pass, once the pools hold the plans this load needs
+        sat = [Request(r.rid, 0.0, r.key, r.n_points) for r in reqs if n_warm <= r.rid < n_requests]
+        srv.run(sat)
+        dsat, _ = srv.run(sat)
+        ss = summarize(dsat, lambda rid: npts[rid])
+        s["saturated"] = {"points_per_s": ss["points_per_s"], "p50_ms": ss["p50_ms"], "p99_ms": ss["p99_ms"]}
+        srv.close()
+        out[name] = s
+    out["config"] = {"workload": "serve_poisson200", "requests_timed": n_requests - n_warm, "warmup": n_warm,
+                     "shapes": len(shapes), "hbm_budget_gb": 120, "streams": 16,
+                     "latency": "arrival to result in pinned host memory"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +333,8 @@ def main():
                     help="FFT length per axis at the interval levels (0 = library default)")
     ap.add_argument("--near-kernel", type=int, default=0, help="level-0 product kernel variant (0 = default)")
     ap.add_argument("--interval-kernel", type=int, default=0, help="interval product kernel variant (0 = default)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-solve batched workload")
+    ap.add_argument("--no-serve", action="store_true", help="skip the Poisson-arrival serving workload")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -392,6 +514,10 @@ def main():
                                          "kernel spectra precomputed outside the timing)"}
         out["rel_err_fp32_vs_oracle"] = fmm.rel_linf(got, uref)
         out["rel_err_fp64_vs_oracle"] = fmm.rel_linf(u64.double().cpu().numpy(), uref)
+    if world == 1 and not args.no_batch:
+        out["batch"] = batch_run(torch, lgfm, max(3, min(200, args.steps // 10)), 3, flush)
+    if world == 1 and not args.no_serve:
+        out["serve"] = serve_run(torch, lgfm)
     if rank == 0:
         print(json.dumps(out))
     s32.close()

@@ -131,6 +131,26 @@ lgf_status lgf_plan_create_ex(const int32_t *block_ijk, int64_t n_blocks, int32_
                               int32_t interp_mode, const lgf_plan_options *opts, lgf_plan *out);
 
 /*
+ * lgf_plan_create_multi - one plan over n_problems independent problems that
+ * share n_b, the interpolation order and the precision (batched solves of
+ * uneven domains).  Problem p owns blocks block_offsets[p] ..
+ * block_offsets[p+1]-1 of block_ijk (its own index space: problems may reuse
+ * block indices) and has its own level count n_levels[p].  No list links two
+ * problems, so each problem's u is the one a plan of it alone computes (Sec.
+ * 3.1 applied per problem); the tables of all problems are concatenated, so
+ * one lgf_solve runs one launch per phase for the whole set.
+ *   block_offsets  n_problems + 1 ascending offsets, block_offsets[0] = 0,
+ *                  at least one block per problem
+ *   n_levels       n_problems level counts (each as in lgf_plan_create)
+ *   f and u of lgf_solve: the problems' blocks back to back in this order.
+ * Errors as lgf_plan_create; a problem's own error names the problem.
+ */
+lgf_status lgf_plan_create_multi(const int32_t *block_ijk, const int64_t *block_offsets,
+                                 const int32_t *n_levels, int32_t n_problems, int32_t n_b,
+                                 int32_t interp_order, int32_t precision, int32_t interp_mode,
+                                 const lgf_plan_options *opts, lgf_plan *out);
+
+/*
  * Plan statistics: the work of one solve (Sec. 3.2 counts for this block set).
  *   pairs[l]   level 0: near (block, block) pairs; level l >= 1: interaction-list
  *              (target, source) interval pairs; each costs NW complex products
@@ -139,6 +159,8 @@ lgf_status lgf_plan_create_ex(const int32_t *block_ijk, int64_t n_blocks, int32_
  *   top_product_level  highest level with a non-empty interaction list
  *   merged_level01     1 if levels 0 and 1 share one product pass (nw[1] is
  *                      then the level-0 spectrum size)
+ *   n_problems         independent problems in the plan (lgf_plan_create_multi)
+ *   n_levels           the largest level count of its problems
  */
 #define LGF_MAX_LEVELS 24
 typedef struct {
@@ -150,6 +172,7 @@ typedef struct {
     int64_t nw[LGF_MAX_LEVELS + 1];
     int64_t workspace_bytes;
     int32_t merged_level01;
+    int32_t n_problems;
 } lgf_plan_stats;
 
 lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);
@@ -177,6 +200,26 @@ lgf_status lgf_solve(lgf_plan plan, const void *f_dev, void *u_dev, void *stream
  */
 lgf_status lgf_solve_batch(const lgf_plan *plans, const void *const *f_dev,
                            void *const *u_dev, int32_t n, void *stream);
+
+/*
+ * Batches: many independent solves launched together (batched serving of
+ * uneven problems).  lgf_batch_create records n (plan, f, u) triples; each
+ * lgf_batch_launch forks the stream into a pool of up to 16 streams, runs the
+ * solves round-robin on the pool so they overlap on the device, and joins the
+ * pool back into the stream.  use_graph = 1 captures the whole batch once
+ * into a CUDA graph (after one uncaptured warm-up solve of every plan, during
+ * lgf_batch_create) and each launch replays it.
+ *   plans      n distinct plans (all on the current device); the batch keeps
+ *              pointers to them: destroy the batch before its plans
+ *   f_dev[i], u_dev[i]  device buffers of plan i, fixed for the batch's life
+ * A batch must not be launched again before its previous launch finished
+ * (the plans' workspaces are reused).
+ */
+typedef struct lgf_batch_s *lgf_batch;
+lgf_status lgf_batch_create(const lgf_plan *plans, const void *const *f_dev, void *const *u_dev,
+                            int32_t n, int32_t use_graph, lgf_batch *out);
+lgf_status lgf_batch_launch(lgf_batch batch, void *stream);
+lgf_status lgf_batch_destroy(lgf_batch batch);
 
 /*
  * lgf_solve_host - lgf_solve with host buffers: copies f to the plan's device

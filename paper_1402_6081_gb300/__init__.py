@@ -32,6 +32,9 @@ _SIGS = {
     "lgf_plan_create_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_plan_create_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "lgf_plan_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "lgf_plan_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
@@ -39,6 +42,10 @@ _SIGS = {
     "lgf_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p]),
     "lgf_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lgf_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "lgf_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -119,7 +126,8 @@ class lgf_plan_stats(ctypes.Structure):
                 ("intervals", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("groups", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
-                ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32)]
+                ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32),
+                ("n_problems", ctypes.c_int32)]
 
 
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
@@ -151,6 +159,35 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
     return out.value
 
 
+def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0):
+    opts = lgf_plan_options()
+    opts.fft_size_interval = fft_size_interval
+    opts.near_kernel = near_kernel
+    opts.interval_kernel = interval_kernel
+    opts.single_stream = single_stream
+    opts.separate_level1 = separate_level1
+    return opts
+
+
+def lgf_plan_create_multi(blocks_list, n_b: int, n_levels_list, interp_order: int,
+                          precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE, **options) -> int:
+    """One plan over several independent problems (see include/lgf.h): f and u
+    hold the problems' blocks back to back in list order."""
+    parts = [np.asarray(b, dtype=np.int32).reshape(-1, 3) for b in blocks_list]
+    b = np.ascontiguousarray(np.concatenate(parts, axis=0))
+    offs = np.zeros(len(parts) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum([len(p) for p in parts])
+    lv = np.ascontiguousarray(np.asarray(n_levels_list, dtype=np.int32))
+    if len(lv) != len(parts):
+        raise ValueError("one level count per problem")
+    opts = _options(**options)
+    out = ctypes.c_void_p()
+    _check(library().lgf_plan_create_multi(b.ctypes.data, offs.ctypes.data, lv.ctypes.data, len(parts), n_b,
+                                           interp_order, precision, interp_mode, ctypes.byref(opts),
+                                           ctypes.byref(out)), "lgf_plan_create_multi")
+    return out.value
+
+
 def lgf_plan_get_stats(plan: int) -> dict:
     st = lgf_plan_stats()
     _check(library().lgf_plan_get_stats(plan, ctypes.byref(st)), "lgf_plan_get_stats")
@@ -160,7 +197,7 @@ def lgf_plan_get_stats(plan: int) -> dict:
             "fft_size_interval": st.fft_size_interval, "pairs": list(st.pairs[: L + 1]),
             "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
             "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes,
-            "merged_level01": st.merged_level01}
+            "merged_level01": st.merged_level01, "n_problems": st.n_problems}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:
@@ -187,6 +224,25 @@ def lgf_solve_batch(plans, fs, us, stream=None) -> None:
     F = (ctypes.c_void_p * n)(*[_dev_ptr(f) for f in fs])
     U = (ctypes.c_void_p * n)(*[_dev_ptr(u) for u in us])
     _check(library().lgf_solve_batch(P, F, U, n, _stream_ptr(stream)), "lgf_solve_batch")
+
+
+def lgf_batch_create(plans, fs, us, use_graph: int = 1) -> int:
+    """Batch of independent solves (see include/lgf.h); returns the handle."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*plans)
+    F = (ctypes.c_void_p * n)(*[_dev_ptr(f) for f in fs])
+    U = (ctypes.c_void_p * n)(*[_dev_ptr(u) for u in us])
+    out = ctypes.c_void_p()
+    _check(library().lgf_batch_create(P, F, U, n, use_graph, ctypes.byref(out)), "lgf_batch_create")
+    return out.value
+
+
+def lgf_batch_launch(batch: int, stream=None) -> None:
+    _check(library().lgf_batch_launch(batch, _stream_ptr(stream)), "lgf_batch_launch")
+
+
+def lgf_batch_destroy(batch: int) -> None:
+    _check(library().lgf_batch_destroy(batch), "lgf_batch_destroy")
 
 
 def lgf_solve_host(plan: int, f_host, u_host, stream=None) -> None:
@@ -293,6 +349,74 @@ class Solver:
         if self.plan:
             lgf_destroy(self.plan)
             self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent uneven solves run together.
+
+    Problems sharing (n_b, order) go into one multi-problem plan
+    (lgf_plan_create_multi), so each phase of the method is one launch for all
+    of them; the plans of the different classes run concurrently on a stream
+    pool and, with ``use_graph``, the whole batch is one CUDA graph
+    (lgf_batch_create).  ``problems`` is a list of (blocks, n_b, n_levels,
+    order); ``options`` maps n_b to plan options (e.g. from the autotuner)."""
+
+    def __init__(self, problems, precision: int = LGF_FP32, use_graph: int = 1, options=None):
+        import torch
+        self.precision = precision
+        dt = torch.float64 if precision == LGF_FP64 else torch.float32
+        options = options or {}
+        classes = {}
+        for i, (blocks, n_b, n_levels, order) in enumerate(problems):
+            classes.setdefault((n_b, order), []).append(i)
+        self.plans, self.f, self.u = [], [], []
+        self.where = [None] * len(problems)   # problem -> (class, first point, n points, shape)
+        for c, ((n_b, order), idx) in enumerate(sorted(classes.items())):
+            blocks = [problems[i][0] for i in idx]
+            levels = [problems[i][2] for i in idx]
+            plan = lgf_plan_create_multi(blocks, n_b, levels, order, precision, **options.get(n_b, {}))
+            self.plans.append(plan)
+            n = sum(int(np.asarray(b).reshape(-1, 3).shape[0]) for b in blocks) * n_b ** 3
+            self.f.append(torch.zeros(n, dtype=dt, device="cuda"))
+            self.u.append(torch.empty(n, dtype=dt, device="cuda"))
+            at = 0
+            for i in idx:
+                nb_i = int(np.asarray(problems[i][0]).reshape(-1, 3).shape[0])
+                self.where[i] = (c, at, nb_i * n_b ** 3, (nb_i, n_b, n_b, n_b))
+                at += nb_i * n_b ** 3
+        self.batch = lgf_batch_create(self.plans, self.f, self.u, use_graph)
+
+    def f_view(self, i):
+        c, at, n, shape = self.where[i]
+        return self.f[c][at:at + n].view(shape)
+
+    def u_view(self, i):
+        c, at, n, shape = self.where[i]
+        return self.u[c][at:at + n].view(shape)
+
+    def set_sources(self, fs):
+        for i, f in enumerate(fs):
+            self.f_view(i).copy_(f if hasattr(f, "copy_") else __import__("torch").from_numpy(np.asarray(f)))
+
+    def __call__(self, stream=None):
+        lgf_batch_launch(self.batch, stream)
+
+    def n_points(self) -> int:
+        return sum(int(f.numel()) for f in self.f)
+
+    def close(self):
+        if self.batch:
+            lgf_batch_destroy(self.batch)
+            self.batch = None
+        for p in self.plans:
+            lgf_destroy(p)
+        self.plans = []
 
     def __del__(self):
         try:

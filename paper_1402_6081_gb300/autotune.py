@@ -1,0 +1,133 @@
+"""Autotuner for the solver's scheduling options.
+
+For one problem shape it times every candidate option set on the current GPU
+(CUDA events, a few warm solves each) and keeps the fastest.  The choices only
+change scheduling, never the method: the interval FFT length S_I (any S_I >=
+2 n_I - 1 is exact) and the interaction-kernel variant.  Results are cached
+per (GPU name, n_b, precision, levels, block-count bucket) in a JSON file
+($LGF_TUNE_CACHE, default ~/.cache/paper_1402_6081_gb300/autotune.json).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import pathlib
+import threading
+
+import numpy as np
+
+from . import LGF_FP32
+
+_LOCK = threading.Lock()
+
+CANDIDATES = {
+    4: [{"fft_size_interval": 10, "interval_kernel": 1}],
+    8: [{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (1, 3)],
+    16: [{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (1, 3)],
+}
+
+
+def cache_path() -> pathlib.Path:
+    p = os.environ.get("LGF_TUNE_CACHE")
+    if p:
+        return pathlib.Path(p)
+    return pathlib.Path.home() / ".cache" / "paper_1402_6081_gb300" / "autotune.json"
+
+
+def _key(n_b, precision, n_levels, n_blocks) -> str:
+    import torch
+    dev = torch.cuda.get_device_name(torch.cuda.current_device())
+    bucket = 1 << max(0, int(math.ceil(math.log2(max(1, n_blocks)))))
+    return f"{dev}|nb{n_b}|p{precision}|L{n_levels}|B{bucket}"
+
+
+def _load() -> dict:
+    try:
+        return json.loads(cache_path().read_text())
+    except Exception:
+        return {}
+
+
+def _store(d: dict) -> None:
+    p = cache_path()
+    try:
+        p.parent.mkdir(parents=True, exist_ok=True)
+        tmp = p.with_suffix(f".{os.getpid()}.tmp")
+        tmp.write_text(json.dumps(d, indent=1, sort_keys=True))
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def _time_plan(plan, n_points, dtype, reps, warmup) -> float:
+    import torch
+
+    from . import lgf_solve
+    rng = np.random.default_rng(0)
+    f = torch.from_numpy(rng.uniform(0.0, 1.0, size=n_points)).to(dtype).cuda()
+    u = torch.empty_like(f)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lgf_solve(plan, f, u, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            lgf_solve(plan, f, u, stream)
+        b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def time_options(blocks_list, n_b, levels_list, order, precision, opts, reps=5, warmup=2) -> float:
+    """Mean milliseconds per solve of a (multi-problem) plan with these options."""
+    import torch
+
+    from . import LGF_FP64, lgf_destroy, lgf_plan_create_multi
+    plan = lgf_plan_create_multi(blocks_list, n_b, levels_list, order, precision, **opts)
+    try:
+        npts = sum(int(np.asarray(b).reshape(-1, 3).shape[0]) for b in blocks_list) * n_b ** 3
+        dt = torch.float64 if precision == LGF_FP64 else torch.float32
+        return _time_plan(plan, npts, dt, reps, warmup)
+    finally:
+        lgf_destroy(plan)
+
+
+def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = LGF_FP32,
+               use_cache: bool = True, reps: int = 5) -> dict:
+    """Fastest option set for a set of problems solved as one plan (the cache
+    key is the block size, precision, deepest level count and total blocks,
+    rounded up to a power of two)."""
+    n_blocks = sum(int(np.asarray(b).reshape(-1, 3).shape[0]) for b in blocks_list)
+    key = _key(n_b, precision, max(levels_list), n_blocks) + f"|P{len(blocks_list)}"
+    if use_cache:
+        with _LOCK:
+            hit = _load().get(key)
+        if hit is not None:
+            return dict(hit["options"])
+    cands = CANDIDATES.get(n_b, [{}])
+    if precision != LGF_FP32:
+        cands = [c for c in cands if c.get("interval_kernel", 1) == 1]
+    timings = []
+    for c in cands:
+        try:
+            timings.append((time_options(blocks_list, n_b, levels_list, order, precision, c, reps=reps), c))
+        except Exception:
+            continue
+    if not timings:
+        return {}
+    best_ms, best = min(timings, key=lambda t: t[0])
+    if use_cache:
+        with _LOCK:
+            d = _load()
+            d[key] = {"options": best, "ms": best_ms,
+                      "all": [{"options": c, "ms": t} for t, c in timings]}
+            _store(d)
+    return dict(best)
+
+
+def tune(blocks, n_b: int, n_levels: int, order: int, precision: int = LGF_FP32,
+         use_cache: bool = True, reps: int = 5) -> dict:
+    """Fastest option set for one problem (from the cache when present)."""
+    return tune_multi([np.asarray(blocks).reshape(-1, 3)], n_b, [n_levels], order, precision, use_cache, reps)

@@ -34,6 +34,9 @@ void fft_lines(std::complex<double>* base, int n, int stride, int count, int64_t
 // Spectrum (NW values, w = (kz*S + ky)*NX + kx, scaled by 1/S^3) of the kernel
 // vector k(m) = G(h (m - d n_b)), |m_a| <= n - 1, placed at m mod S; tab is the
 // dense |offset| table G(h*(a,b,c)) of edge V + 1.
+// per-kernel timing capacity of a plan (0 when timing is off)
+int plan_timing_capacity(const lgf_plan_s* plan);
+
 void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
                      std::complex<double>* outw);
 

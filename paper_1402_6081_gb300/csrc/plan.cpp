@@ -282,6 +282,7 @@ struct lgf_plan_s {
     int device = 0;
     int n_b = 0, n_I = 0, L = 0, n_max = 0, prec = LGF_FP32;
     int64_t n_blocks = 0, n_points = 0;
+    int n_problems = 1;
     int S0 = 0, SI = 0, Lmac = 0;
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     int single_stream = 0;
@@ -370,9 +371,30 @@ static lgf_status ensure_twiddles(int device, int prec) {
     return ok();
 }
 
-static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
-    const int nb = P->n_b, nI = P->n_I, L = P->L;
-    const int64_t NB = P->n_blocks;
+// One problem's tree, lists and item tables, with group, slot and block
+// indices local to the problem.  A plan holds one or more problems: their
+// tables are concatenated level by level with offsets, and since no list
+// links two problems, each problem's result is the one it has alone.
+struct HostLevel {
+    int n_groups = 0;
+    bool m2l = false;                          // interaction list not empty (level 0: near field, always)
+    std::vector<int> gn;                       // n_groups x 27 neighbour groups, -1 = none
+    std::vector<R2CItem> r2c;                  // src: block (l <= 1) or slot (l >= 2); dst: slot
+    std::vector<int> iv_slot;                  // slot of each interval
+    std::vector<int> reg_child, reg_parent;    // l >= 2: 8 children per parent (block at l = 2, else slot)
+    std::vector<int> int_slot, int_parent;     // 1 <= l < Lmac
+};
+
+struct HostPlan {
+    int L = 0, Lmac = 0;
+    int64_t n_blocks = 0;
+    std::vector<HostLevel> lev;                // levels 0..Lmac
+    std::vector<int64_t> pairs, intervals, groups;   // levels 0..L
+};
+
+static lgf_status build_host(const int32_t* ijk, int64_t NB, int L, HostPlan& H) {
+    H.L = L;
+    H.n_blocks = NB;
     std::vector<I3> blocks(static_cast<size_t>(NB));
     std::unordered_map<uint64_t, int> bidx;
     for (int64_t b = 0; b < NB; ++b) {
@@ -434,14 +456,15 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
     // interaction lists: sizes per level (level 0: near pairs); Lmac is the
     // highest level whose interaction list is not empty
     int Lmac = 0;
-    P->pairs.assign(size_t(L) + 1, 0);
-    P->intervals.assign(size_t(L) + 1, 0);
-    P->groups.assign(size_t(L) + 1, 0);
-    for (int l = 0; l <= L; ++l) P->intervals[size_t(l)] = int64_t(lv[size_t(l)].iv.size());
+    H.pairs.assign(size_t(L) + 1, 0);
+    H.intervals.assign(size_t(L) + 1, 0);
+    H.groups.assign(size_t(L) + 1, 0);
+    std::vector<bool> m2l(size_t(L) + 1, false);
+    for (int l = 0; l <= L; ++l) H.intervals[size_t(l)] = int64_t(lv[size_t(l)].iv.size());
     for (const I3& a : lv[0].iv)
         for (int e = 0; e < 27; ++e) {
             const I3 q{a[0] + e % 3 - 1, a[1] + (e / 3) % 3 - 1, a[2] + e / 9 - 1};
-            P->pairs[0] += lv[0].iv_index.count(pack(q));
+            H.pairs[0] += lv[0].iv_index.count(pack(q));
         }
     for (int l = 1; l < L; ++l) {
         const auto& L_ = lv[size_t(l)];
@@ -455,11 +478,11 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
                 if (!near(a, q) && L_.iv_index.count(pack(q))) ++n;
             }
         }
-        P->pairs[size_t(l)] = n;
-        lv[size_t(l)].m2l = n > 0;
+        H.pairs[size_t(l)] = n;
+        m2l[size_t(l)] = n > 0;
         if (n > 0) Lmac = l;
     }
-    P->Lmac = Lmac;
+    H.Lmac = Lmac;
     // sibling groups and slots for levels 0..Lmac
     for (int l = 0; l <= Lmac; ++l) {
         auto& L_ = lv[size_t(l)];
@@ -474,18 +497,99 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         std::sort(L_.groups.begin(), L_.groups.end(),
                   [&](const I3& a, const I3& b) { return morton(a, lo) < morton(b, lo); });
         for (size_t i = 0; i < L_.groups.size(); ++i) L_.group_index[pack(L_.groups[i])] = int(i);
-        P->groups[size_t(l)] = int64_t(L_.groups.size());
+        H.groups[size_t(l)] = int64_t(L_.groups.size());
     }
-    // ---- device objects ----
+    // item tables
+    H.lev.resize(size_t(Lmac) + 1);
+    for (int l = 0; l <= Lmac; ++l) {
+        const auto& L_ = lv[size_t(l)];
+        HostLevel& T = H.lev[size_t(l)];
+        T.n_groups = int(L_.groups.size());
+        T.m2l = l == 0 || m2l[size_t(l)];
+        T.gn.assign(size_t(T.n_groups) * 27, -1);
+        for (int g = 0; g < T.n_groups; ++g)
+            for (int e = 0; e < 27; ++e) {
+                const I3& G = L_.groups[size_t(g)];
+                I3 q{G[0] + e % 3 - 1, G[1] + (e / 3) % 3 - 1, G[2] + e / 9 - 1};
+                auto it = L_.group_index.find(pack(q));
+                if (it != L_.group_index.end()) T.gn[size_t(g) * 27 + e] = it->second;
+            }
+        for (size_t i = 0; i < L_.iv.size(); ++i) {
+            const int slot = L_.slot(L_.iv[i]);
+            T.iv_slot.push_back(slot);
+            T.r2c.push_back({l <= 1 ? int(i) : slot, slot});
+        }
+        if (l >= 2) {
+            const auto& Lc = lv[size_t(l) - 1];
+            for (const I3& a : L_.iv) {
+                T.reg_parent.push_back(L_.slot(a));
+                const int cg = Lc.group_index.at(pack(a));
+                for (int c = 0; c < 8; ++c) {
+                    const I3 q{2 * a[0] + (c & 1), 2 * a[1] + ((c >> 1) & 1), 2 * a[2] + (c >> 2)};
+                    auto it = Lc.iv_index.find(pack(q));
+                    if (it == Lc.iv_index.end()) T.reg_child.push_back(-1);
+                    else T.reg_child.push_back(l == 2 ? it->second : cg * 8 + c);
+                }
+            }
+        }
+        if (l >= 1 && l < Lmac) {
+            const auto& Lp = lv[size_t(l) + 1];
+            for (const I3& a : L_.iv) {
+                T.int_slot.push_back(L_.slot(a));
+                T.int_parent.push_back(Lp.slot(parent_of(a)));
+            }
+        }
+    }
+    return ok();
+}
+
+// Concatenates the problems' tables level by level and builds the device
+// workspace.  A problem takes part in levels 0..its own Lmac; at a level where
+// another problem has an interaction list but it has none, its products are
+// exact zeros (all its pairs sit at near offsets, whose kernel is zero), so its
+// result is unchanged.
+static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
+    const int nb = P->n_b, nI = P->n_I;
+    const size_t np = hp.size();
+    int L = 0, Lmac = 0;
+    for (const HostPlan& H : hp) {
+        L = std::max(L, H.L);
+        Lmac = std::max(Lmac, H.Lmac);
+    }
+    P->L = L;
+    P->Lmac = Lmac;
+    P->pairs.assign(size_t(L) + 1, 0);
+    P->intervals.assign(size_t(L) + 1, 0);
+    P->groups.assign(size_t(L) + 1, 0);
+    for (const HostPlan& H : hp)
+        for (int l = 0; l <= H.L; ++l) {
+            P->pairs[size_t(l)] += H.pairs[size_t(l)];
+            P->intervals[size_t(l)] += H.intervals[size_t(l)];
+            P->groups[size_t(l)] += H.groups[size_t(l)];
+        }
+    // offsets: blocks per problem, groups per (level, problem); -1 = absent
+    std::vector<int> boff(np, 0);
+    for (size_t p = 1; p < np; ++p) boff[p] = boff[p - 1] + int(hp[p - 1].n_blocks);
+    std::vector<std::vector<int>> goff(size_t(Lmac) + 1, std::vector<int>(np, -1));
+    std::vector<int> ngroups(size_t(Lmac) + 1, 0);
+    for (int l = 0; l <= Lmac; ++l)
+        for (size_t p = 0; p < np; ++p)
+            if (l <= hp[p].Lmac) {
+                goff[size_t(l)][p] = ngroups[size_t(l)];
+                ngroups[size_t(l)] += hp[p].lev[size_t(l)].n_groups;
+            }
     const size_t elem = P->prec == LGF_FP64 ? sizeof(double) : sizeof(float);
     const size_t cplx = 2 * elem;
     const size_t n3 = size_t(nI) * nI * nI;
     P->lev.resize(size_t(Lmac) + 1);
     for (int l = 0; l <= Lmac; ++l) {
-        const auto& L_ = lv[size_t(l)];
+        const auto& go = goff[size_t(l)];
         DevLevel& D = P->lev[size_t(l)];
-        D.n_groups = int(L_.groups.size());
-        D.m2l = (l == 0) || (L_.m2l && !(l == 1 && P->merged));
+        D.n_groups = ngroups[size_t(l)];
+        bool any = false;
+        for (size_t p = 0; p < np; ++p)
+            if (go[p] >= 0) any = any || hp[p].lev[size_t(l)].m2l;
+        D.m2l = (l == 0) || (any && !(l == 1 && P->merged));
         const size_t slots = size_t(D.n_groups) * 8;
         lgf_status s;
         if (D.m2l) {
@@ -493,14 +597,15 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
             const size_t NWS = size_t(nws_of(S));
             if ((s = dalloc(P, slots * NWS * cplx, &D.fh, true)) != LGF_OK) return s;
             if ((s = dalloc(P, slots * NWS * cplx, &D.uh, false)) != LGF_OK) return s;
-            std::vector<int> gn(size_t(D.n_groups) * 27, -1);
-            for (int g = 0; g < D.n_groups; ++g)
-                for (int e = 0; e < 27; ++e) {
-                    const I3& G = L_.groups[size_t(g)];
-                    I3 q{G[0] + e % 3 - 1, G[1] + (e / 3) % 3 - 1, G[2] + e / 9 - 1};
-                    auto it = L_.group_index.find(pack(q));
-                    if (it != L_.group_index.end()) gn[size_t(g) * 27 + e] = it->second;
-                }
+            std::vector<int> gn;
+            std::vector<R2CItem> items;
+            for (size_t p = 0; p < np; ++p) {
+                if (go[p] < 0) continue;
+                const HostLevel& T = hp[p].lev[size_t(l)];
+                for (int v : T.gn) gn.push_back(v >= 0 ? v + go[p] : -1);
+                for (const R2CItem& it : T.r2c)
+                    items.push_back({l <= 1 ? it.src + boff[p] : it.src + 8 * go[p], it.dst + 8 * go[p]});
+            }
             if ((s = upload(P, gn, &D.gnbr)) != LGF_OK) return s;
             {
                 std::vector<int> cnt(size_t(D.n_groups), 0), ord(size_t(D.n_groups));
@@ -510,11 +615,6 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
                 }
                 std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cnt[size_t(a)] > cnt[size_t(b)]; });
                 if ((s = upload(P, ord, &D.order)) != LGF_OK) return s;
-            }
-            std::vector<R2CItem> items;
-            for (size_t i = 0; i < L_.iv.size(); ++i) {
-                const int slot = L_.slot(L_.iv[i]);
-                items.push_back({l <= 1 ? int(i) : slot, slot});
             }
             D.n_r2c = int(items.size());
             if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
@@ -526,9 +626,9 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
             if ((s = dalloc(P, slots * n3 * elem, &D.ut, true)) != LGF_OK) return s;
             if (D.m2l) {
                 std::vector<C2RItem> items;
-                for (const I3& a : L_.iv) {
-                    const int slot = L_.slot(a);
-                    items.push_back({slot, slot, -1});
+                for (size_t p = 0; p < np; ++p) {
+                    if (go[p] < 0) continue;
+                    for (int slot : hp[p].lev[size_t(l)].iv_slot) items.push_back({slot + 8 * go[p], slot + 8 * go[p], -1});
                 }
                 D.n_c2r = int(items.size());
                 if ((s = upload(P, items, &D.c2r)) != LGF_OK) return s;
@@ -536,41 +636,42 @@ static lgf_status build_plan(lgf_plan_s* P, const int32_t* ijk) {
         }
         if (l >= 2) {
             if ((s = dalloc(P, slots * n3 * elem, &D.ft, true)) != LGF_OK) return s;
-            const auto& Lc = lv[size_t(l) - 1];
             std::vector<int> child, par;
-            for (const I3& a : L_.iv) {
-                par.push_back(L_.slot(a));
-                const int cg = Lc.group_index.at(pack(a));
-                for (int c = 0; c < 8; ++c) {
-                    const I3 q{2 * a[0] + (c & 1), 2 * a[1] + ((c >> 1) & 1), 2 * a[2] + (c >> 2)};
-                    auto it = Lc.iv_index.find(pack(q));
-                    if (it == Lc.iv_index.end()) child.push_back(-1);
-                    else child.push_back(l == 2 ? it->second : cg * 8 + c);
-                }
+            for (size_t p = 0; p < np; ++p) {
+                if (go[p] < 0) continue;
+                const HostLevel& T = hp[p].lev[size_t(l)];
+                for (int v : T.reg_parent) par.push_back(v + 8 * go[p]);
+                for (int c : T.reg_child)
+                    child.push_back(c < 0 ? -1 : l == 2 ? c + boff[p] : c + 8 * goff[size_t(l) - 1][p]);
             }
             D.n_reg = int(par.size());
             if ((s = upload(P, child, &D.reg_child)) != LGF_OK) return s;
             if ((s = upload(P, par, &D.reg_parent)) != LGF_OK) return s;
         }
         if (l >= 1 && l < Lmac) {
-            const auto& Lp = lv[size_t(l) + 1];
             std::vector<int> sl, pa;
-            for (const I3& a : L_.iv) {
-                sl.push_back(L_.slot(a));
-                pa.push_back(Lp.slot(parent_of(a)));
+            for (size_t p = 0; p < np; ++p) {
+                if (go[p] < 0 || l >= hp[p].Lmac) continue;
+                const HostLevel& T = hp[p].lev[size_t(l)];
+                for (int v : T.int_slot) sl.push_back(v + 8 * go[p]);
+                for (int v : T.int_parent) pa.push_back(v + 8 * goff[size_t(l) + 1][p]);
             }
             D.n_int = int(sl.size());
             if ((s = upload(P, sl, &D.int_slot)) != LGF_OK) return s;
             if ((s = upload(P, pa, &D.int_parent)) != LGF_OK) return s;
         }
     }
-    // level-0 output items: block b from its level-0 slot, plus level-1 field
+    // level-0 output items: block b from its level-0 slot, plus its level-1
+    // field (same slot number within the problem, level-1 group offset)
     {
         std::vector<C2RItem> items;
-        for (int64_t b = 0; b < NB; ++b) {
-            const int slot = lv[0].slot(blocks[size_t(b)]);
-            const bool has_ut1 = P->merged ? Lmac >= 2 : Lmac >= 1;
-            items.push_back({slot, int(b), has_ut1 ? slot : -1});
+        for (size_t p = 0; p < np; ++p) {
+            const HostPlan& H = hp[p];
+            const bool has_ut1 = P->merged ? H.Lmac >= 2 : H.Lmac >= 1;
+            const std::vector<int>& s0 = H.lev[0].iv_slot;
+            for (int64_t b = 0; b < H.n_blocks; ++b)
+                items.push_back({s0[size_t(b)] + 8 * goff[0][p], int(b) + boff[p],
+                                 has_ut1 ? s0[size_t(b)] + 8 * goff[1][p] : -1});
         }
         P->n_out = int(items.size());
         lgf_status s = upload(P, items, &P->out_items);
@@ -749,6 +850,8 @@ static lgf_status check_device(const lgf_plan_s* P) {
     return ok();
 }
 
+int plan_timing_capacity(const lgf_plan_s* plan) { return int(plan->ev.size() / 2); }
+
 }  // namespace lgf
 
 using namespace lgf;
@@ -771,16 +874,25 @@ lgf_status lgf_plan_create(const int32_t* block_ijk, int64_t n_blocks, int32_t n
                               nullptr, out);
 }
 
-lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_t n_b, int32_t n_levels,
-                              int32_t interp_order, int32_t precision, int32_t interp_mode,
-                              const lgf_plan_options* opts, lgf_plan* out) {
+static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, const int32_t* n_levels,
+                              int32_t n_problems, int32_t n_b, int32_t interp_order, int32_t precision,
+                              int32_t interp_mode, const lgf_plan_options* opts, lgf_plan* out) {
     if (!out) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: out is NULL");
     *out = nullptr;
-    if (!block_ijk || n_blocks < 1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need n_blocks >= 1 block indices");
+    if (!block_ijk || !offsets || !n_levels || n_problems < 1)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need block indices and at least one problem");
+    if (offsets[0] != 0) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create_multi: block_offsets[0] must be 0");
+    for (int32_t p = 0; p < n_problems; ++p) {
+        if (offsets[p + 1] - offsets[p] < 1)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need n_blocks >= 1 block indices (problem " +
+                                                 std::to_string(p) + ")");
+        if (n_levels[p] < 1 || n_levels[p] > 24)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 1 <= n_levels <= 24");
+    }
+    const int64_t n_blocks = offsets[n_problems];
     if (n_blocks > (int64_t(1) << 26)) return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: more than 2^26 blocks");
     if (n_b != 4 && n_b != 8 && n_b != 16)
         return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: n_b must be 4, 8 or 16");
-    if (n_levels < 1 || n_levels > 24) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 1 <= n_levels <= 24");
     if (interp_order < 0 || interp_order + 1 > n_b + 1)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
@@ -792,10 +904,10 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     P->n_b = n_b;
     P->n_I = n_b + 1;
-    P->L = n_levels;
     P->n_max = interp_order + 1;
     P->prec = precision;
     P->n_blocks = n_blocks;
+    P->n_problems = n_problems;
     P->n_points = n_blocks * int64_t(n_b) * n_b * n_b;
     P->S0 = s_level0(n_b);
     P->SI = s_interval(n_b);
@@ -816,13 +928,38 @@ lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
-    s = build_plan(P.get(), block_ijk);
+    std::vector<HostPlan> hp(static_cast<size_t>(n_problems));
+    for (int32_t p = 0; p < n_problems; ++p) {
+        s = build_host(block_ijk + 3 * offsets[p], offsets[p + 1] - offsets[p], n_levels[p], hp[size_t(p)]);
+        if (s != LGF_OK) {
+            if (n_problems > 1) fail(s, "problem " + std::to_string(p) + ": " + g_err);
+            return s;
+        }
+    }
+    s = build_plan(P.get(), hp);
     if (s != LGF_OK) return s;
     for (auto& a : P->aux) LGF_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
     LGF_CUDA(cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming));
     for (auto& j : P->join) LGF_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
     *out = P.release();
     return ok();
+}
+
+lgf_status lgf_plan_create_ex(const int32_t* block_ijk, int64_t n_blocks, int32_t n_b, int32_t n_levels,
+                              int32_t interp_order, int32_t precision, int32_t interp_mode,
+                              const lgf_plan_options* opts, lgf_plan* out) {
+    if (!out) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: out is NULL");
+    *out = nullptr;
+    if (!block_ijk || n_blocks < 1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need n_blocks >= 1 block indices");
+    const int64_t offsets[2] = {0, n_blocks};
+    return create_plan(block_ijk, offsets, &n_levels, 1, n_b, interp_order, precision, interp_mode, opts, out);
+}
+
+lgf_status lgf_plan_create_multi(const int32_t* block_ijk, const int64_t* block_offsets, const int32_t* n_levels,
+                                 int32_t n_problems, int32_t n_b, int32_t interp_order, int32_t precision,
+                                 int32_t interp_mode, const lgf_plan_options* opts, lgf_plan* out) {
+    return create_plan(block_ijk, block_offsets, n_levels, n_problems, n_b, interp_order, precision, interp_mode,
+                       opts, out);
 }
 
 lgf_status lgf_plan_workspace_bytes(lgf_plan plan, size_t* bytes) {
@@ -850,6 +987,7 @@ lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
         if (l <= plan->Lmac && plan->lev[size_t(l)].m2l) st->nw[l] = nw_of(l == 0 ? plan->S0 : plan->SI);
     }
     st->merged_level01 = plan->merged ? 1 : 0;
+    st->n_problems = plan->n_problems;
     if (plan->merged && plan->Lmac >= 1) st->nw[1] = nw_of(plan->S0);
     size_t b = 0;
     lgf_plan_workspace_bytes(plan, &b);

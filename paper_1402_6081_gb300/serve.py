@@ -1,0 +1,271 @@
+"""Continuous-batching solve server.
+
+Requests (a block-structured domain and its source) arrive over time.  The
+server keeps plans resident in pools keyed by problem shape, admits an arrived
+request as soon as a plan for its shape is idle or a new one fits the HBM
+budget (evicting idle plans of other shapes if needed), and runs it on one of
+a pool of CUDA streams: host-to-device copy of f, the solve, device-to-host
+copy of u, a completion event.  Requests that arrive while others run are
+admitted as plans and memory free up, so their work overlaps on the device.
+Latency is measured from arrival to completion of the copy of u.
+
+The admission logic runs on the host and takes a plan factory and a
+submit/poll pair, so it runs the same with fake plans on a simulated clock.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the run
+    key: tuple              # problem shape (n_b, blocks per axis, ...)
+    n_points: int
+
+
+@dataclasses.dataclass
+class Done:
+    rid: int
+    arrival: float
+    start: float
+    finish: float
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+class AdmissionError(RuntimeError):
+    pass
+
+
+class _Slot:
+    """One resident plan with its device and pinned host buffers."""
+
+    def __init__(self, key, handle, nbytes):
+        self.key = key
+        self.handle = handle
+        self.nbytes = nbytes
+        self.busy = False
+        self.last_used = 0.0
+
+
+class PlanPools:
+    """Plans per shape under an HBM budget.  make(key) -> (handle, bytes);
+    drop(handle) frees one."""
+
+    def __init__(self, make, drop, budget_bytes: float):
+        self.make = make
+        self.drop = drop
+        self.budget = float(budget_bytes)
+        self.used = 0.0
+        self.slots: dict = collections.defaultdict(list)
+        self.known: dict = {}               # shape -> bytes of its plan
+
+    def acquire(self, key, now: float, need_bytes=None):
+        """An idle plan of this shape, else a new one if it fits the budget
+        (evicting idle plans, least recently used first), else None (wait).
+        The size of a new plan is the one measured for this shape before, else
+        need_bytes; with neither, the plan is made and then checked."""
+        for s in self.slots[key]:
+            if not s.busy:
+                s.busy = True
+                s.last_used = now
+                return s
+        est = self.known.get(key, need_bytes)
+        if est is not None:
+            if est > self.budget:
+                raise AdmissionError(f"request {key} needs {est:.3e} B, above the budget {self.budget:.3e} B")
+            if not self._make_room(est):
+                return None
+        handle, nbytes = self.make(key)
+        self.known[key] = nbytes
+        if self.used + nbytes > self.budget and not self._make_room(nbytes):
+            self.drop(handle)
+            if nbytes > self.budget:
+                raise AdmissionError(f"request {key} needs {nbytes:.3e} B, above the budget {self.budget:.3e} B")
+            return None
+        s = _Slot(key, handle, nbytes)
+        s.busy = True
+        s.last_used = now
+        self.slots[key].append(s)
+        self.used += nbytes
+        return s
+
+    def _make_room(self, nbytes) -> bool:
+        idle = sorted((s for ss in self.slots.values() for s in ss if not s.busy), key=lambda s: s.last_used)
+        while self.used + nbytes > self.budget and idle:
+            self._evict(idle.pop(0))
+        return self.used + nbytes <= self.budget
+
+    def release(self, slot, now: float):
+        slot.busy = False
+        slot.last_used = now
+
+    def _evict(self, slot):
+        self.slots[slot.key].remove(slot)
+        self.used -= slot.nbytes
+        self.drop(slot.handle)
+
+    def close(self):
+        for ss in self.slots.values():
+            for s in ss:
+                self.drop(s.handle)
+        self.slots.clear()
+        self.used = 0.0
+
+
+def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter, max_inflight: int = 64,
+               need_bytes=None, idle_wait: float = 20e-6, sleep=time.sleep):
+    """Drive a request stream.  submit(slot, request) starts the work and
+    returns a token; poll(token) -> bool says whether it finished.
+    need_bytes(key) (optional) estimates a new plan's bytes before creating it.
+    Returns the list of Done records and the rejected request ids."""
+    pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    inflight = []
+    done, rejected = [], []
+    t0 = clock()
+    while pending or inflight:
+        now = clock() - t0
+        progressed = False
+        while pending and pending[0].arrival <= now and len(inflight) < max_inflight:
+            r = pending[0]
+            try:
+                slot = pools.acquire(r.key, now, need_bytes(r.key) if need_bytes else None)
+            except AdmissionError:
+                pending.popleft()
+                rejected.append(r.rid)
+                progressed = True
+                continue
+            if slot is None:
+                break                       # wait for memory or a plan of this shape
+            pending.popleft()
+            start = clock() - t0
+            inflight.append((r, slot, submit(slot, r), start))
+            progressed = True
+        still = []
+        for item in inflight:
+            r, slot, tok, start = item
+            if poll(tok):
+                fin = clock() - t0
+                done.append(Done(r.rid, r.arrival, start, fin))
+                pools.release(slot, fin)
+                progressed = True
+            else:
+                still.append(item)
+        inflight = still
+        if not progressed:
+            if pending and not inflight and pending[0].arrival > now:
+                sleep(min(pending[0].arrival - now, 1e-3))
+            else:
+                sleep(idle_wait)
+    return done, rejected
+
+
+def summarize(done, n_points_of) -> dict:
+    lat = np.array([d.latency for d in done]) * 1e3
+    t_first = min(d.arrival for d in done)
+    t_last = max(d.finish for d in done)
+    pts = sum(n_points_of(d.rid) for d in done)
+    return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max()), "points_per_s": pts / (t_last - t_first),
+            "span_s": t_last - t_first}
+
+
+class GpuServer:
+    """The CUDA side: plans per shape, device buffers, pinned host buffers and
+    a pool of streams.  problems maps a shape key to a workloads-style problem
+    (blocks, n_b, n_levels, order, f); source(request) optionally gives the
+    request's own pinned host source (default: the shape's f)."""
+
+    def __init__(self, precision: int, problems: dict, budget_bytes: float = 120e9, n_streams: int = 16,
+                 tuned_options=None, source=None, keep_results: bool = False):
+        import torch
+
+        import paper_1402_6081_gb300 as lgfm
+        self.torch = torch
+        self.lgfm = lgfm
+        self.precision = precision
+        self.dtype = torch.float64 if precision == lgfm.LGF_FP64 else torch.float32
+        self.problems = problems
+        self.tuned = tuned_options or {}
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.next_stream = 0
+        self.source = source
+        self.host_f = {} if source else {k: torch.from_numpy(p.f).to(self.dtype).pin_memory()
+                                         for k, p in problems.items()}
+        self.keep_results = keep_results
+        self.results = {}
+        self.bytes_per_point = {}           # n_b -> largest plan bytes per point seen
+        self.pools = PlanPools(self._make, self._drop, budget_bytes)
+
+    def points(self, key) -> int:
+        p = self.problems[key]
+        return len(p.blocks) * p.n_b ** 3
+
+    def need_bytes(self, key):
+        """Size of a new plan of this shape: measured before for the shape, else
+        scaled from the plans of the same block size (25% margin), else unknown."""
+        if key in self.pools.known:
+            return self.pools.known[key]
+        r = self.bytes_per_point.get(self.problems[key].n_b)
+        return None if r is None else 1.25 * r * self.points(key)
+
+    def _make(self, key):
+        p = self.problems[key]
+        opts = self.tuned.get(key, {})
+        s = self.lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, self.precision, **opts)
+        shape = (len(p.blocks), p.n_b, p.n_b, p.n_b)
+        f = self.torch.empty(shape, dtype=self.dtype, device="cuda")
+        u = self.torch.empty_like(f)
+        uh = self.torch.empty(shape, dtype=self.dtype).pin_memory()
+        nbytes = s.workspace_bytes() + 2 * f.numel() * f.element_size()
+        r = nbytes / self.points(key)
+        self.bytes_per_point[p.n_b] = max(r, self.bytes_per_point.get(p.n_b, 0.0))
+        return (s, f, u, uh), nbytes
+
+    def _drop(self, handle):
+        s, f, u, uh = handle
+        self.torch.cuda.synchronize()
+        s.close()
+
+    def submit(self, slot, req):
+        s, f, u, uh = slot.handle
+        st = self.streams[self.next_stream]
+        self.next_stream = (self.next_stream + 1) % len(self.streams)
+        src = self.source(req) if self.source else self.host_f[req.key]
+        with self.torch.cuda.stream(st):
+            f.copy_(src, non_blocking=True)
+            s(f, u, st)
+            uh.copy_(u, non_blocking=True)
+            ev = self.torch.cuda.Event()
+            ev.record(st)
+        return (ev, uh, req.rid)
+
+    def poll(self, tok):
+        if not tok[0].query():
+            return False
+        if self.keep_results:
+            self.results[tok[2]] = tok[1].numpy().copy()
+        return True
+
+    def warm(self, keys):
+        """One resident plan per shape, made before the stream starts."""
+        slots = [self.pools.acquire(k, 0.0, self.need_bytes(k)) for k in keys]
+        for sl in slots:
+            if sl is not None:
+                self.pools.release(sl, 0.0)
+
+    def run(self, requests, **kw):
+        return run_stream(requests, self.pools, self.submit, self.poll, need_bytes=self.need_bytes, **kw)
+
+    def close(self):
+        self.torch.cuda.synchronize()
+        self.pools.close()

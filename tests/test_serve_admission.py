@@ -1,0 +1,130 @@
+"""Host logic of the solve server: admission under the HBM budget, plan reuse
+and eviction, overlap of requests, latency accounting.  A simulated clock and
+fake plans stand in for the GPU (each fake solve takes a fixed time)."""
+import numpy as np
+import pytest
+
+from paper_1402_6081_gb300.serve import AdmissionError, PlanPools, Request, run_stream, summarize
+
+
+class Sim:
+    def __init__(self, sizes, service):
+        self.t = 0.0
+        self.sizes = sizes            # key -> plan bytes
+        self.service = service        # key -> seconds per solve
+        self.live = {}
+        self.used = 0
+        self.max_used = 0
+        self.made = 0
+        self.running = 0
+        self.max_running = 0
+        self.next = 0
+
+    def clock(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-6)
+
+    def make(self, key):
+        self.made += 1
+        h = self.next
+        self.next += 1
+        self.live[h] = self.sizes[key]
+        self.used += self.sizes[key]
+        self.max_used = max(self.max_used, self.used)
+        return h, self.sizes[key]
+
+    def drop(self, h):
+        self.used -= self.live.pop(h)
+
+    def submit(self, slot, req):
+        self.running += 1
+        self.max_running = max(self.max_running, self.running)
+        return [self.t + self.service[req.key], False]
+
+    def poll(self, tok):
+        if self.t >= tok[0] and not tok[1]:
+            tok[1] = True
+            self.running -= 1
+        return tok[1]
+
+
+def _requests(keys, rate, n, seed=0):
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    return [Request(i, float(t[i]), keys[int(rng.integers(len(keys)))], 1000) for i in range(n)]
+
+
+def test_all_served_within_budget_with_plan_reuse():
+    sim = Sim({"a": 30, "b": 50, "c": 20}, {"a": 2e-3, "b": 5e-3, "c": 1e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=400)
+    reqs = _requests(["a", "b", "c"], rate=2000.0, n=300)
+    done, rejected = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep,
+                                need_bytes=lambda k: sim.sizes[k])
+    assert not rejected and len(done) == 300
+    assert sorted(d.rid for d in done) == list(range(300))
+    assert sim.max_used <= 400
+    assert sim.made <= 60                      # plans are kept and reused (>= 80% of requests)
+    assert sim.max_running > 1                 # arrivals overlap running work
+    for d in done:
+        assert d.arrival <= d.start <= d.finish
+
+
+def test_oversize_request_is_rejected_and_others_run():
+    sim = Sim({"a": 30, "huge": 1000}, {"a": 1e-3, "huge": 1e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=100)
+    reqs = [Request(0, 0.0, "a", 1), Request(1, 0.001, "huge", 1), Request(2, 0.002, "a", 1)]
+    done, rejected = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep,
+                                need_bytes=lambda k: sim.sizes[k])
+    assert rejected == [1]
+    assert sim.made == 1                       # the oversize plan is never made
+    assert sorted(d.rid for d in done) == [0, 2]
+    assert sim.max_used <= 100
+    with pytest.raises(AdmissionError):
+        pools.acquire("huge", 0.0, need_bytes=1000)
+
+
+def test_idle_plans_of_other_shapes_are_evicted():
+    sim = Sim({"a": 60, "b": 60}, {"a": 1e-3, "b": 1e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=100)
+    reqs = [Request(i, 0.01 * i, "ab"[i % 2], 1) for i in range(10)]
+    done, rejected = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep,
+                                need_bytes=lambda k: sim.sizes[k])
+    assert len(done) == 10 and not rejected
+    assert sim.max_used <= 100
+    assert sim.made == 10                      # each switch evicts the idle plan of the other shape
+
+
+def test_request_waits_for_memory_instead_of_failing():
+    # two concurrent "a" requests need two plans but only one fits: the second waits
+    sim = Sim({"a": 60}, {"a": 5e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=100)
+    reqs = [Request(0, 0.0, "a", 1), Request(1, 1e-4, "a", 1)]
+    done, rejected = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep)
+    assert not rejected
+    d = {x.rid: x for x in done}
+    assert d[1].start >= d[0].finish - 1e-9
+    assert sim.made == 1
+
+
+def test_latency_equals_service_time_without_queueing():
+    sim = Sim({"a": 10}, {"a": 2e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=100)
+    reqs = [Request(i, 0.01 * i, "a", 100) for i in range(20)]
+    done, _ = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep)
+    s = summarize(done, lambda rid: 100)
+    assert s["requests"] == 20
+    assert abs(s["p50_ms"] - 2.0) < 0.1 and abs(s["p99_ms"] - 2.0) < 0.1
+
+
+def test_sizes_learned_from_the_first_plan_of_a_shape():
+    # without estimates only the first plan of each shape may be made before
+    # its size is known; later ones are admitted against the learned size
+    sim = Sim({"a": 30, "b": 50, "c": 20}, {"a": 2e-3, "b": 5e-3, "c": 1e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=400)
+    reqs = _requests(["a", "b", "c"], rate=2000.0, n=300, seed=4)
+    done, rejected = run_stream(reqs, pools, sim.submit, sim.poll, clock=sim.clock, sleep=sim.sleep)
+    assert len(done) == 300 and not rejected
+    assert pools.known == {"a": 30, "b": 50, "c": 20}
+    assert pools.used <= 400
