@@ -80,6 +80,10 @@ extern "C" lgf_status lgf_batch_create(const lgf_plan* plans, const void* const*
         if (!plans[i] || !f_dev[i] || !u_dev[i]) return fail(LGF_ERR_INVALID_ARG, "lgf_batch_create: NULL entry");
         for (int32_t j = 0; j < i; ++j)
             if (plans[i] == plans[j]) return fail(LGF_ERR_INVALID_ARG, "lgf_batch_create: plans must be distinct");
+        // timing events recorded inside a capture belong to the graph and
+        // cannot be read back per launch
+        if (use_graph && plan_timing_capacity(plans[i]) > 0)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_batch_create: turn plan timing off before capturing a graph");
     }
     auto B = std::make_unique<lgf_batch_s>();
     cudaError_t e = cudaGetDevice(&B->device);

@@ -287,6 +287,46 @@ __global__ void __launch_bounds__(256) k_mac_level0(const cx<T>* __restrict__ fh
 // with zeros at the 27 near ones (|d| <= 1), which removes the list test.
 // The CTA stages the coefficients of its 32 frequencies in shared memory
 // (343 x 32), shared by its G groups.
+// mbarrier and bulk-copy helpers (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Waits for the phase with this parity to complete; false after about 2^32
+// SM cycles (~2 s), far beyond any copy of this kernel.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity))
+        if (clock64() - t0 > (1LL << 32)) return false;
+    return true;
+}
+// bytes (multiple of 16) from global to this CTA's shared memory, both 16-byte
+// aligned; completion counted on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 constexpr int kMacWarps = 12;
 
 // One warp's walk over the (group, neighbour) pairs it owns: groups
@@ -363,6 +403,29 @@ __device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], 
         }
 }
 
+// The 343 coefficient rows of the frequencies w0 .. w0+31 into shared memory
+// ([343][32], zero past NW): eight independent loads per thread in flight
+// before their stores, so a CTA keeps enough requests outstanding to stream.
+template <typename T, int64_t NW, int64_t NWS, int NT>
+__device__ __forceinline__ void stage_coefficients(cx<T>* __restrict__ sk, const cx<T>* __restrict__ kh, int64_t w0,
+                                                   int tid) {
+    constexpr int kTotal = 343 * 32, kBatch = 8;
+    for (int base = 0; base < kTotal; base += kBatch * NT) {
+        cx<T> v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int i = base + j * NT + tid;
+            const int64_t w = w0 + (i & 31);
+            v[j] = (i < kTotal && w < NW) ? ldg_cx(kh + int64_t(i >> 5) * NWS + w) : czero<T>();
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int i = base + j * NT + tid;
+            if (i < kTotal) sk[i] = v[j];
+        }
+    }
+}
+
 // Groups are visited in the plan's work order (sorted by neighbour count, so
 // the warps of one CTA carry similar work).  With include_self the group's own
 // sibling block e = 13 is a source too: that is the merged level-0 / level-1
@@ -380,11 +443,7 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < 343 * 32; i += 32 * kMacWarps) {
-        const int d = i >> 5, lane = i & 31;
-        const int64_t w = w0 + lane;
-        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
-    }
+    stage_coefficients<T, NW, NWS, 32 * kMacWarps>(sk, kh, w0, tid);
     __syncthreads();
     const int g0 = blockIdx.x * groups_per_cta;
     const int g1 = min(n_groups, g0 + groups_per_cta);
@@ -718,11 +777,7 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < 343 * 32; i += 32 * kMacPWarps) {
-        const int d = i >> 5, lane = i & 31;
-        const int64_t w = w0 + lane;
-        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
-    }
+    stage_coefficients<T, NW, NWS, 32 * kMacPWarps>(sk, kh, w0, tid);
     __syncthreads();
     const int g0 = blockIdx.x * groups_per_cta;
     const int g1 = min(n_groups, g0 + groups_per_cta);
@@ -768,6 +823,161 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
             if (gb >= 0) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) uh[(int64_t(gb) * 8 + c) * NWS + w] = accB[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent interaction kernel (FP32).  The same sums as k_mac_interval, with
+// one CTA per SM working through a contiguous range of units (frequency chunk
+// of 32, group position) fixed at plan time so every CTA carries the same
+// number of (group, source) pairs.  The 343 coefficient rows of a chunk
+// (87.8 KB) arrive in shared memory by bulk copies (cp.async.bulk, completion
+// on an mbarrier) into one of two buffers, so the next chunk loads while the
+// current one is used; warps take groups of the current chunk from a shared
+// counter, and the last warp to finish a chunk refills its buffer with the
+// chunk after next.  Each group's sources come from a flat list (source group,
+// centre coefficient row), so the inner loop has no neighbour-mask logic.
+constexpr int kPersistWarps = 24;
+
+__device__ __forceinline__ PairSrc ldg_pair(const PairSrc* p) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(p));
+    return {v.x, v.y};
+}
+
+template <int S>
+__device__ __forceinline__ void persist_load(cx<float> (&F)[8], const cx<float>* __restrict__ fh, int src,
+                                             int64_t wc) {
+    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
+    const cx<float>* p = fh + int64_t(src) * (8 * NWS) + wc;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c] = ldg_cx(p + c * NWS);
+}
+
+// the 8 x 8 sibling products of one source group; kb: centre row of this lane
+__device__ __forceinline__ void persist_block(cx<float> (&acc)[8], const cx<float> (&F)[8],
+                                              const cx<float>* kb) {
+    cx<float> kk[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = kb[(dx + 7 * dy + 49 * dz) * 32];
+#pragma unroll
+    for (int ct = 0; ct < 8; ++ct)
+#pragma unroll
+        for (int cs = 0; cs < 8; ++cs) {
+            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
+            acc[ct] = cmac(acc[ct], F[cs], kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
+        }
+}
+
+constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
+constexpr size_t kPersistSmem = 2 * size_t(kPersistBuf) + 64;
+
+template <int S>
+__global__ void __launch_bounds__(32 * kPersistWarps, 1)
+    k_mac_persist(const cx<float>* __restrict__ fh, const cx<float>* __restrict__ kh, cx<float>* __restrict__ uh,
+                  const PairSrc* __restrict__ pairs, const int* __restrict__ start, const int* __restrict__ order,
+                  const long long* __restrict__ cta_units, int n_groups, int* __restrict__ err) {
+    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
+    constexpr int64_t NWS = (NW + 31) / 32 * 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][343][32]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * kPersistBuf);   // [2]
+    int* ctr = reinterpret_cast<int*>(full + 2);                             // [2] next position
+    int* done = ctr + 2;                                                     // [2] warps finished
+    const long long u0 = cta_units[blockIdx.x], u1 = cta_units[blockIdx.x + 1];
+    if (u0 >= u1) return;
+    const long long c0 = u0 / n_groups, c1 = (u1 - 1) / n_groups;
+    const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        ctr[0] = ctr[1] = 0;
+        done[0] = done[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // one warp issues the 343 row copies of chunk c (256 bytes each)
+    auto fill = [&](long long c) {
+        const int b = int((c - c0) & 1);
+        cx<float>* dst = buf + b * (343 * 32);
+        if (lane == 0) mbar_expect_tx(&full[b], kPersistBuf);
+        __syncwarp();
+        const cx<float>* src = kh + c * 32;
+        for (int d = lane; d < 343; d += 32) bulk_g2s(dst + d * 32, src + int64_t(d) * NWS, 256u, &full[b]);
+    };
+    if (warp == 0) {
+        fill(c0);
+        if (c1 > c0) fill(c0 + 1);
+    }
+    for (long long c = c0; c <= c1; ++c) {
+        const int b = int((c - c0) & 1);
+        if (!mbar_wait(&full[b], unsigned(((c - c0) >> 1) & 1))) {
+            if (lane == 0) atomicExch(err, 1);
+            return;
+        }
+        const cx<float>* sk = buf + b * (343 * 32) + lane;
+        const int pb = c == c0 ? int(u0 % n_groups) : 0;
+        const int pe = c == c1 ? int((u1 - 1) % n_groups) + 1 : n_groups;
+        const int64_t w = c * 32 + lane;
+        const int64_t wc = w < NW ? w : NW - 1;
+        while (true) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&ctr[b], 1);
+            const int pos = pb + __shfl_sync(0xffffffffu, k, 0);
+            if (pos >= pe) break;
+            const int p0 = __ldg(start + pos), p1 = __ldg(start + pos + 1);
+            cx<float> acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = czero<float>();
+            if (p1 > p0) {
+                cx<float> Fa[8], Fb[8];
+                PairSrc pa = ldg_pair(pairs + p0), pq{0, 0};
+                persist_load<S>(Fa, fh, pa.src, wc);
+                for (int p = p0;; p += 2) {
+                    const bool hb = p + 1 < p1;
+                    if (hb) {
+                        pq = ldg_pair(pairs + p + 1);
+                        persist_load<S>(Fb, fh, pq.src, wc);
+                    }
+                    persist_block(acc, Fa, sk + pa.centre * 32);
+                    if (!hb) break;
+                    const bool ha = p + 2 < p1;
+                    if (ha) {
+                        pa = ldg_pair(pairs + p + 2);
+                        persist_load<S>(Fa, fh, pa.src, wc);
+                    }
+                    persist_block(acc, Fb, sk + pq.centre * 32);
+                    if (!ha) break;
+                }
+            }
+            if (w < NW) {
+                cx<float>* out = uh + int64_t(__ldg(order + pos)) * (8 * NWS) + w;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) out[i * NWS] = acc[i];
+            }
+        }
+        // this warp is done with chunk c; the last one out refills the buffer
+        // with chunk c + 2 (every read of the buffer has completed by then)
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&done[b], 1) == kPersistWarps - 1;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+            if (lane == 0) {
+                ctr[b] = 0;
+                done[b] = 0;
+            }
+            if (c + 2 <= c1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fill(c + 2);
             }
         }
     }
@@ -897,12 +1107,119 @@ __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ chil
     }
 }
 
+// Reg, wide form (FP32; FP64 keeps k_reg, whose registers it would exceed):
+// one CTA of kRegThreads per parent takes all 8 children at once.  z pass first: item (cx, cy, x, y) reads the z lines of its two
+// children (cz = 0, 1; coalesced along x) and sums their adjoint products into
+// a[cx][cy][pz][y][x]; y pass: item (cx, pz, x) sums the two cy lines into
+// b[cx][pz][py][x]; x pass: item (pz, py) sums the two cx lines into the
+// parent row, staged through shared memory for coalesced stores.  b and the
+// staged rows reuse a's storage (every pass reads into registers, then a
+// barrier, then writes; each pass has at most one item per thread where it
+// writes in place).
+constexpr int kRegThreads = 768;   // >= 2 * 17 * 17 (one y-pass item per thread)
+
+template <typename T, int NI>
+__host__ __device__ constexpr size_t reg_wide_smem() { return sizeof(T) * 4 * size_t(NI) * NI * NI; }
+
+template <typename T, int NI>
+__global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ child_src, int child_is_block,
+                                                          const int* __restrict__ child_index,
+                                                          const int* __restrict__ parent_slot,
+                                                          T* __restrict__ dst, const InterpW<T, NI> W) {
+    constexpr int NB = NI - 1, N2 = NI * NI, N3 = NI * NI * NI;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* a = reinterpret_cast<T*>(smem_raw);   // [4][NI][NI][NI] = [cx + 2cy][pz][y][x]
+    const int t = threadIdx.x;
+    // z pass (4 N2 items, a thread may take two)
+    for (int it = t; it < 4 * N2; it += kRegThreads) {
+        const int x = it % NI, y = (it / NI) % NI, cxy = it / N2;
+        T out[NI];
+#pragma unroll
+        for (int p = 0; p < NI; ++p) out[p] = T(0);
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz) {
+            const int s = __ldg(child_index + blockIdx.x * 8 + cxy + 4 * cz);
+            if (s < 0) continue;
+            T in[NI], o[NI];
+            if (child_is_block) {
+                const bool live = x < NB && y < NB;
+                const T* col = child_src + int64_t(s) * NB * NB * NB + y * NB + x;
+#pragma unroll
+                for (int z = 0; z < NI; ++z) in[z] = (live && z < NB) ? __ldg(col + z * NB * NB) : T(0);
+            } else {
+                const T* col = child_src + int64_t(s) * N3 + y * NI + x;
+#pragma unroll
+                for (int z = 0; z < NI; ++z) in[z] = __ldg(col + z * N2);
+            }
+            apply_wt(W, cz, in, o);
+#pragma unroll
+            for (int p = 0; p < NI; ++p) out[p] += o[p];
+        }
+#pragma unroll
+        for (int p = 0; p < NI; ++p) a[(cxy * NI + p) * N2 + y * NI + x] = out[p];
+    }
+    __syncthreads();
+    // y pass: 2 N2 items (cx, pz, x) <= kRegThreads, b[cx][pz][py][x] over a
+    T yout[NI];
+    const bool ya = t < 2 * N2;
+    if (ya) {
+        const int x = t % NI, pz = (t / NI) % NI, cx = t / N2;
+#pragma unroll
+        for (int p = 0; p < NI; ++p) yout[p] = T(0);
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy) {
+            T in[NI], o[NI];
+            const T* col = a + ((cx + 2 * cy) * NI + pz) * N2 + x;
+#pragma unroll
+            for (int y = 0; y < NI; ++y) in[y] = col[y * NI];
+            apply_wt(W, cy, in, o);
+#pragma unroll
+            for (int p = 0; p < NI; ++p) yout[p] += o[p];
+        }
+    }
+    __syncthreads();
+    if (ya) {
+        const int x = t % NI, pz = (t / NI) % NI, cx = t / N2;
+#pragma unroll
+        for (int p = 0; p < NI; ++p) a[((cx * NI + pz) * NI + p) * NI + x] = yout[p];
+    }
+    __syncthreads();
+    // x pass: N2 items (pz, py); rows staged in a, then stored coalesced
+    T xout[NI];
+    const bool xa = t < N2;
+    if (xa) {
+        const int py = t % NI, pz = t / NI;
+#pragma unroll
+        for (int p = 0; p < NI; ++p) xout[p] = T(0);
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+            T in[NI], o[NI];
+            const T* row = a + ((cx * NI + pz) * NI + py) * NI;
+#pragma unroll
+            for (int x = 0; x < NI; ++x) in[x] = row[x];
+            apply_wt(W, cx, in, o);
+#pragma unroll
+            for (int p = 0; p < NI; ++p) xout[p] += o[p];
+        }
+    }
+    __syncthreads();
+    if (xa) {
+#pragma unroll
+        for (int p = 0; p < NI; ++p) a[t * NI + p] = xout[p];
+    }
+    __syncthreads();
+    T* o = dst + int64_t(__ldg(parent_slot + blockIdx.x)) * N3;
+    for (int i = t; i < N3; i += kRegThreads) o[i] = a[i];
+}
+
 // Interp: u[slot] += (W_cz x W_cy x W_cx) up[parent], c = slot & 7.
+// With block != nullptr the output is the child's first NI-1 nodes per axis,
+// added into u at block[i] * (NI-1)^3 (a level-1 interval's block points).
 template <typename T, int NI>
 __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__ slot,
                                                          const int* __restrict__ parent, T* __restrict__ u,
                                                          const T* __restrict__ up, const InterpW<T, NI> W,
-                                                         int accumulate) {
+                                                         int accumulate, const int* __restrict__ block) {
     constexpr int N2 = NI * NI, N3 = NI * NI * NI;
     __shared__ T a[N3];
     const int t = threadIdx.x;
@@ -939,6 +1256,16 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
 #pragma unroll
         for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
         apply_w(W, czp, in, out);
+        if (block) {
+            constexpr int NB = NI - 1;
+            const int ix = t % NI, iy = t / NI;
+            if (ix < NB && iy < NB) {
+                T* o = u + int64_t(__ldg(block + blockIdx.x)) * NB * NB * NB + iy * NB + ix;
+#pragma unroll
+                for (int z = 0; z < NB; ++z) o[z * NB * NB] += out[z];
+            }
+            return;
+        }
         T* o = u + int64_t(s) * N3 + t;
         if (accumulate) {
 #pragma unroll
@@ -1098,6 +1425,36 @@ cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, co
 #undef LGF_MACI
 }
 
+template <int S>
+static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp,
+                                      cudaStream_t st) {
+    auto kern = dev::k_mac_persist<S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::kPersistSmem));
+    if (e != cudaSuccess) return e;
+    if (pp.n_groups == 0 || pp.n_cta == 0) return cudaSuccess;
+    kern<<<pp.n_cta, 32 * dev::kPersistWarps, dev::kPersistSmem, st>>>(
+        static_cast<const dev::cx<float>*>(fh), static_cast<const dev::cx<float>*>(kh),
+        static_cast<dev::cx<float>*>(uh), pp.pairs, pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
+                                   cudaStream_t st) {
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+#define LGF_MACP(SS) \
+    case SS: return launch_mac_persist<SS>(fh, kh, uh, pp, st);
+        switch (S) {
+            LGF_MACP(8) LGF_MACP(10) LGF_MACP(16) LGF_MACP(17) LGF_MACP(18) LGF_MACP(32) LGF_MACP(33) LGF_MACP(34)
+            LGF_MACP(36)
+            default: return cudaErrorInvalidValue;
+        }
+#undef LGF_MACP
+    }
+}
+
 template <typename T, int NI>
 static dev::InterpW<T, NI> pack_w(const T* W) {
     dev::InterpW<T, NI> p;
@@ -1113,11 +1470,20 @@ cudaError_t Launch<T>::reg(int n_b, int /*n_max*/, const T* child_src, int child
                            const int* child_index, const int* parent_slot, int n_parents, T* dst,
                            const T* W, cudaStream_t st) {
     if (n_parents == 0) return cudaSuccess;
-#define LGF_REG(NI)                                                                                   \
-    if (n_b + 1 == NI) {                                                                              \
+#define LGF_REG(NI)                                                                                     \
+    if (n_b + 1 == NI && sizeof(T) == 8) {                                                              \
         dev::k_reg<T, NI><<<n_parents, dev::kLineThreads, 0, st>>>(child_src, child_is_block, child_index, \
                                                                   parent_slot, dst, pack_w<T, NI>(W));  \
-        return cudaGetLastError();                                                                    \
+        return cudaGetLastError();                                                                      \
+    }                                                                                                   \
+    if (n_b + 1 == NI) {                                                                                \
+        constexpr size_t smem = dev::reg_wide_smem<T, NI>();                                           \
+        auto kern = dev::k_reg_wide<T, NI>;                                                             \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+        if (e != cudaSuccess) return e;                                                                 \
+        kern<<<n_parents, dev::kRegThreads, smem, st>>>(child_src, child_is_block, child_index, parent_slot, \
+                                                        dst, pack_w<T, NI>(W));                         \
+        return cudaGetLastError();                                                                      \
     }
     LGF_REG(5) LGF_REG(9) LGF_REG(17)
 #undef LGF_REG
@@ -1126,12 +1492,12 @@ cudaError_t Launch<T>::reg(int n_b, int /*n_max*/, const T* child_src, int child
 
 template <typename T>
 cudaError_t Launch<T>::interp(int n_b, const int* slot, const int* parent, int n_items, T* u,
-                              const T* up, const T* W, int accumulate, cudaStream_t st) {
+                              const T* up, const T* W, int accumulate, const int* block, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
 #define LGF_INTERP(NI)                                                                                      \
     if (n_b + 1 == NI) {                                                                                    \
         dev::k_interp<T, NI><<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W),    \
-                                                                   accumulate);                            \
+                                                                   accumulate, block);                     \
         return cudaGetLastError();                                                                          \
     }
     LGF_INTERP(5) LGF_INTERP(9) LGF_INTERP(17)

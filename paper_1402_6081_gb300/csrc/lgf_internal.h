@@ -34,11 +34,11 @@ void fft_lines(std::complex<double>* base, int n, int stride, int count, int64_t
 // Spectrum (NW values, w = (kz*S + ky)*NX + kx, scaled by 1/S^3) of the kernel
 // vector k(m) = G(h (m - d n_b)), |m_a| <= n - 1, placed at m mod S; tab is the
 // dense |offset| table G(h*(a,b,c)) of edge V + 1.
-// per-kernel timing capacity of a plan (0 when timing is off)
-int plan_timing_capacity(const lgf_plan_s* plan);
-
 void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double* tab, int V,
                      std::complex<double>* outw);
+
+// per-kernel timing capacity of a plan (0 when timing is off)
+int plan_timing_capacity(const lgf_plan_s* plan);
 
 // ---- interpolation stencils (plan.cpp) ----
 // W[c][i][p] (2 x n_I x n_I) for child c node i and parent node p.
@@ -62,6 +62,21 @@ inline int64_t nws_of(int S) { return (nw_of(S) + 31) / 32 * 32; }
 struct R2CItem { int src; int dst; };      // source index -> spectrum slot
 struct C2RItem { int src; int dst; int aux; };
 
+// Work lists of the persistent interaction kernel: per group, in work order,
+// its source groups with the coefficient row of their centre offset d = 2e
+// (row (dx+3) + 7 (dy+3) + 49 (dz+3) of the 7^3 table); the launch's units
+// (frequency chunk * n_groups + position) split into n_cta ranges of about
+// equal work; err is set when a wait in the kernel runs out.
+struct PairSrc { int src; int centre; };
+struct PersistPlan {
+    const PairSrc* pairs = nullptr;
+    const int* start = nullptr;          // n_groups + 1 offsets into pairs
+    const int* order = nullptr;          // group id per position
+    const long long* cta_units = nullptr;    // n_cta + 1
+    int n_groups = 0, n_cta = 0;
+    int* err = nullptr;
+};
+
 // Launchers (kernels.cu); T = float or double.  All asynchronous on `stream`.
 template <typename T>
 struct Launch {
@@ -81,13 +96,18 @@ struct Launch {
     // include_self: the group's own block is a source (merged levels 0 and 1)
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, int include_self, cudaStream_t st);
+    // The same products as mac_interval from a persistent kernel (one CTA per
+    // SM) that stages the coefficient chunks with bulk copies; FP32 only.
+    static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
+                                   cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,
                            const int* child_index, const int* parent_slot, int n_parents,
                            T* dst, const T* W, cudaStream_t st);
-    // u[slot] (+)= Interp(u_parent[parent]) for each item (accumulate: add, else store).
+    // u[slot] (+)= Interp(u_parent[parent]) for each item (accumulate: add, else
+    // store); with block != nullptr: u[block[i]] += the first n_b nodes per axis.
     static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items,
-                              T* u, const T* up, const T* W, int accumulate, cudaStream_t st);
+                              T* u, const T* up, const T* W, int accumulate, const int* block, cudaStream_t st);
 };
 
 }  // namespace lgf

@@ -272,8 +272,10 @@ struct DevLevel {
     int n_reg = 0;
     int* int_slot = nullptr;
     int* int_parent = nullptr;
+    int* int_block = nullptr;       // level 1: the block of each item (output into the blocks)
     int n_int = 0;
     std::shared_ptr<SpecEntry> kh;
+    PersistPlan pp;                 // work lists of the persistent products (FP32)
 };
 
 }  // namespace lgf
@@ -286,6 +288,7 @@ struct lgf_plan_s {
     int S0 = 0, SI = 0, Lmac = 0;
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     int single_stream = 0;
+    int* err = nullptr;                 // device flag: a bounded wait in a kernel ran out
     // levels 0 and 1 share the block grid and S0 = 2 n_b suffices for the
     // first n_b nodes of a level-1 interval: their products are summed into
     // one spectrum per block (one inverse FFT, no level-1 transforms)
@@ -309,7 +312,10 @@ struct lgf_plan_s {
     // the level-1 chain and the level >= 2 chain run on their own streams,
     // forked from and joined into the caller's stream
     cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    // join[0]: level-1 chain done; join[1]: levels >= 2 (or their upward part)
+    // done; join[2]: level-0 products done; join[3]: level-0 inverse FFT done;
+    // join[4]: levels >= 2 downward part done
+    cudaEvent_t fork = nullptr, join[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     ~lgf_plan_s() {
         int cur = 0;
@@ -391,6 +397,69 @@ struct HostPlan {
     std::vector<HostLevel> lev;                // levels 0..Lmac
     std::vector<int64_t> pairs, intervals, groups;   // levels 0..L
 };
+
+// Whether level l's products run in the persistent kernel: FP32 plans with
+// interval_kernel 4 (or the default 0), at the interval levels and at level 0
+// when it carries the merged level-0/level-1 products.  Its 24 warps share the
+// groups of one frequency chunk, so by default a level needs at least 48
+// groups (fewer leave warps idle; the one-CTA-per-chunk form is faster there).
+static bool uses_persist(const lgf_plan_s* P, int l) {
+    if (P->prec != LGF_FP32) return false;
+    if (P->interval_kernel != 0 && P->interval_kernel != 4) return false;
+    if (l == 0 && !P->merged) return false;
+    return P->interval_kernel == 4 || P->lev[size_t(l)].n_groups >= 48;
+}
+
+// Work lists of the persistent kernel for one level (see PersistPlan).
+static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<int>& gn, const std::vector<int>& ord,
+                                int S, bool include_self) {
+    const int G = D.n_groups;
+    std::vector<PairSrc> pairs;
+    std::vector<int> start(size_t(G) + 1, 0);
+    for (int pos = 0; pos < G; ++pos) {
+        const int g = ord[size_t(pos)];
+        for (int e = 0; e < 27; ++e) {
+            const int q = gn[size_t(g) * 27 + e];
+            if (q < 0 || (e == 13 && !include_self)) continue;
+            const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
+            pairs.push_back({q, (2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)});
+        }
+        start[size_t(pos) + 1] = int(pairs.size());
+    }
+    int n_sm = 0;
+    LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
+    const long long chunks = nws_of(S) / 32, n_cta = std::max(1, n_sm);
+    // unit weight: its pairs plus one for the group's set-up and stores
+    std::vector<long long> pre(size_t(G) + 1, 0);
+    for (int pos = 0; pos < G; ++pos) pre[size_t(pos) + 1] = pre[size_t(pos)] + (start[size_t(pos) + 1] - start[size_t(pos)]) + 1;
+    const long long Wg = pre[size_t(G)], Wt = Wg * chunks;
+    std::vector<long long> cut(size_t(n_cta) + 1);
+    for (long long b = 0; b <= n_cta; ++b) {
+        const long long T = (Wt * b) / n_cta;
+        const long long c = std::min(T / Wg, chunks);
+        const long long rem = T - c * Wg;
+        const long long pos = std::lower_bound(pre.begin(), pre.end(), rem) - pre.begin();
+        cut[size_t(b)] = std::min(c * G + std::min<long long>(pos, G), chunks * G);
+    }
+    cut[0] = 0;
+    cut[size_t(n_cta)] = chunks * G;
+    for (size_t b = 1; b < cut.size(); ++b) cut[b] = std::max(cut[b], cut[b - 1]);
+    lgf_status s;
+    PairSrc* dp = nullptr;
+    int* ds = nullptr;
+    long long* dc = nullptr;
+    if ((s = upload(P, pairs, &dp)) != LGF_OK) return s;
+    if ((s = upload(P, start, &ds)) != LGF_OK) return s;
+    if ((s = upload(P, cut, &dc)) != LGF_OK) return s;
+    D.pp.pairs = dp;
+    D.pp.start = ds;
+    D.pp.order = D.order;
+    D.pp.cta_units = dc;
+    D.pp.n_groups = G;
+    D.pp.n_cta = int(n_cta);
+    D.pp.err = P->err;
+    return ok();
+}
 
 static lgf_status build_host(const int32_t* ijk, int64_t NB, int L, HostPlan& H) {
     H.L = L;
@@ -581,6 +650,12 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
     const size_t elem = P->prec == LGF_FP64 ? sizeof(double) : sizeof(float);
     const size_t cplx = 2 * elem;
     const size_t n3 = size_t(nI) * nI * nI;
+    {
+        void* e = nullptr;
+        lgf_status s = dalloc(P, sizeof(int), &e, true);
+        if (s != LGF_OK) return s;
+        P->err = static_cast<int*>(e);
+    }
     P->lev.resize(size_t(Lmac) + 1);
     for (int l = 0; l <= Lmac; ++l) {
         const auto& go = goff[size_t(l)];
@@ -615,6 +690,7 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                 }
                 std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cnt[size_t(a)] > cnt[size_t(b)]; });
                 if ((s = upload(P, ord, &D.order)) != LGF_OK) return s;
+                if (uses_persist(P, l) && (s = build_persist(P, D, gn, ord, S, l == 0)) != LGF_OK) return s;
             }
             D.n_r2c = int(items.size());
             if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
@@ -649,16 +725,20 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             if ((s = upload(P, par, &D.reg_parent)) != LGF_OK) return s;
         }
         if (l >= 1 && l < Lmac) {
-            std::vector<int> sl, pa;
+            std::vector<int> sl, pa, bl;
             for (size_t p = 0; p < np; ++p) {
                 if (go[p] < 0 || l >= hp[p].Lmac) continue;
                 const HostLevel& T = hp[p].lev[size_t(l)];
                 for (int v : T.int_slot) sl.push_back(v + 8 * go[p]);
                 for (int v : T.int_parent) pa.push_back(v + 8 * goff[size_t(l) + 1][p]);
+                // level-1 intervals are the problem's blocks, in block order
+                if (l == 1)
+                    for (size_t i = 0; i < T.int_slot.size(); ++i) bl.push_back(boff[p] + int(i));
             }
             D.n_int = int(sl.size());
             if ((s = upload(P, sl, &D.int_slot)) != LGF_OK) return s;
             if ((s = upload(P, pa, &D.int_parent)) != LGF_OK) return s;
+            if (l == 1 && (s = upload(P, bl, &D.int_block)) != LGF_OK) return s;
         }
     }
     // level-0 output items: block b from its level-0 slot, plus its level-1
@@ -727,52 +807,24 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     const int Lm = P->Lmac;
     const bool conc = !P->single_stream;
     cudaStream_t s1 = conc ? P->aux[0] : st, s2 = conc ? P->aux[1] : st;
+    // The persistent level-0 kernel holds every SM until it ends, and anything
+    // running beside it delays it.  With it, levels >= 2 are split: the upward
+    // part (Reg, forward FFTs) runs beside the level-0 forward FFT, the
+    // downward part (products, inverse FFTs, interpolation) beside the level-0
+    // inverse FFT, and the level-2 field is finally interpolated straight into
+    // the blocks.  Otherwise levels >= 2 run beside the level-0 products and
+    // their level-1 field is added by the level-0 inverse FFT.
+    const bool split = Lm >= 2 && uses_persist(P, 0);
+    auto record = [&](int k, cudaStream_t s) { return conc ? cudaEventRecord(P->join[k], s) : cudaSuccess; };
+    auto wait = [&](cudaStream_t s, int k) { return conc ? cudaStreamWaitEvent(s, P->join[k], 0) : cudaSuccess; };
     // fork: the other chains start after all prior work on the caller's stream
     if (conc && (Lm >= 2 || (Lm >= 1 && !P->merged))) {
         LGF_CUDA(cudaEventRecord(P->fork, st));
         if (!P->merged) LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
         if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
     }
-    // ---- level 0 on the caller's stream: forward FFT, near-field products
-    e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
-    if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
-    if (P->merged) {
-        e = timed(P, "mac_level01", st, [&] {
-            return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
-                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, st);
-        });
-    } else {
-        e = timed(P, "mac_level0", st, [&] {
-            return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
-                                  P->near_kernel, st);
-        });
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "near-field products");
-    // ---- level 1 on s1: forward FFT, products, inverse FFT into u~1 (merged
-    // form: already part of the level-0 products)
-    if (Lm >= 1 && !P->merged) {
-        DevLevel& D = lev[1];
-        if (D.m2l) {
-            e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
-            if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
-            e = timed(P, "mac_interval_l1", s1, [&] {
-                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
-                                        0, s1);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
-            e = timed(P, "c2r_interval", s1, [&] {
-                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s1);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
-        } else {
-            e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), s1);
-            if (e != cudaSuccess) return cuda_fail(e, "clear level field");
-        }
-        if (conc) LGF_CUDA(cudaEventRecord(P->join[0], s1));
-    }
-    // ---- levels >= 2 on s2: Reg + forward FFTs upward, products, then inverse
-    // FFTs and interpolation downward to level 2
-    if (Lm >= 2) {
+    // ---- levels >= 2 upward on s2: Reg from the level below, forward FFT
+    auto up_part = [&]() -> lgf_status {
         for (int l = 2; l <= Lm; ++l) {
             DevLevel& D = lev[size_t(l)];
             const bool from_blocks = l == 2;
@@ -788,10 +840,15 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                 if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
             }
         }
+        return ok();
+    };
+    // ---- levels >= 2 on s2: products, inverse FFTs and interpolation down to level 2
+    auto down_part = [&]() -> lgf_status {
         for (int l = 2; l <= Lm; ++l) {
             DevLevel& D = lev[size_t(l)];
             if (!D.m2l) continue;
             e = timed(P, "mac_interval_l2plus", s2, [&] {
+                if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s2);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
                                         0, s2);
             });
@@ -811,23 +868,95 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             if (l < Lm) {
                 e = timed(P, "interp", s2, [&] {
                     return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, 1, s2);
+                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, 1, nullptr, s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interpolation");
             }
         }
-        if (conc) LGF_CUDA(cudaEventRecord(P->join[1], s2));
+        return ok();
+    };
+    lgf_status r;
+    if (split) {
+        if ((r = up_part()) != LGF_OK) return r;
+        LGF_CUDA(record(1, s2));
+    }
+    // ---- level 0 on the caller's stream: forward FFT, near-field products
+    e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
+    if (split) LGF_CUDA(wait(st, 1));
+    if (P->merged) {
+        e = timed(P, "mac_level01", st, [&] {
+            if (uses_persist(P, 0)) return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, st);
+            return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
+                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, st);
+        });
+    } else {
+        e = timed(P, "mac_level0", st, [&] {
+            return Lc::mac_level0(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0,
+                                  P->near_kernel, st);
+        });
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "near-field products");
+    if (split) {
+        // downward part after the level-0 products, beside the level-0 inverse FFT
+        LGF_CUDA(record(2, st));
+        LGF_CUDA(wait(s2, 2));
+        if ((r = down_part()) != LGF_OK) return r;
+        e = timed(P, "c2r_level0", st, [&] {
+            return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, nullptr, nI, n3, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "level-0 inverse FFT");
+        LGF_CUDA(record(3, st));
+        LGF_CUDA(wait(s2, 3));
+        DevLevel& D = lev[1];
+        e = timed(P, "interp", s2, [&] {
+            return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, u, static_cast<const T*>(lev[2].ut), W, 1,
+                              D.int_block, s2);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+        LGF_CUDA(record(4, s2));
+        LGF_CUDA(wait(st, 4));
+        return ok();
+    }
+    // ---- level 1 on s1: forward FFT, products, inverse FFT into u~1 (merged
+    // form: already part of the level-0 products)
+    if (Lm >= 1 && !P->merged) {
+        DevLevel& D = lev[1];
+        if (D.m2l) {
+            e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
+            if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
+            e = timed(P, "mac_interval_l1", s1, [&] {
+                if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s1);
+                return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
+                                        0, s1);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
+            e = timed(P, "c2r_interval", s1, [&] {
+                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s1);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
+        } else {
+            e = cudaMemsetAsync(D.ut, 0, sizeof(T) * size_t(D.n_groups) * 8 * size_t(n3), s1);
+            if (e != cudaSuccess) return cuda_fail(e, "clear level field");
+        }
+        LGF_CUDA(record(0, s1));
+    }
+    // ---- levels >= 2 on s2 beside the products
+    if (Lm >= 2) {
+        if ((r = up_part()) != LGF_OK) return r;
+        if ((r = down_part()) != LGF_OK) return r;
+        LGF_CUDA(record(1, s2));
     }
     // ---- join, interpolate level 2 into level 1, and the level-0 output
-    if (conc && Lm >= 1 && !P->merged) LGF_CUDA(cudaStreamWaitEvent(st, P->join[0], 0));
+    if (Lm >= 1 && !P->merged) LGF_CUDA(wait(st, 0));
     if (Lm >= 2) {
-        if (conc) LGF_CUDA(cudaStreamWaitEvent(st, P->join[1], 0));
+        LGF_CUDA(wait(st, 1));
         DevLevel& D = lev[1];
         // merged form: u~1 holds only the interpolated level-2 field (stored);
         // otherwise it already holds the level-1 products' field (added to)
         e = timed(P, "interp", st, [&] {
             return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                              static_cast<const T*>(lev[2].ut), W, P->merged ? 0 : 1, st);
+                              static_cast<const T*>(lev[2].ut), W, P->merged ? 0 : 1, nullptr, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interpolation");
     }
@@ -919,8 +1048,8 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         P->SI = opts->fft_size_interval;
     }
     if (opts) {
-        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 3)
-            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..3");
+        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 4)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..4");
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
         P->single_stream = opts->single_stream != 0;
@@ -1104,6 +1233,14 @@ lgf_status lgf_plan_sync(lgf_plan plan) {
     lgf_status s = check_device(plan);
     if (s != LGF_OK) return s;
     LGF_CUDA(cudaDeviceSynchronize());
+    if (plan->err) {
+        int flag = 0;
+        LGF_CUDA(cudaMemcpy(&flag, plan->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            LGF_CUDA(cudaMemset(plan->err, 0, sizeof(int)));
+            return fail(LGF_ERR_CUDA, "lgf_plan_sync: a wait inside a product kernel ran out (results invalid)");
+        }
+    }
     return ok();
 }
 

@@ -203,7 +203,7 @@ class GpuServer:
                                          for k, p in problems.items()}
         self.keep_results = keep_results
         self.results = {}
-        self.bytes_per_point = {}           # n_b -> largest plan bytes per point seen
+        self.largest = {}                   # n_b -> (points, bytes) of the largest plan made
         self.pools = PlanPools(self._make, self._drop, budget_bytes)
 
     def points(self, key) -> int:
@@ -212,11 +212,12 @@ class GpuServer:
 
     def need_bytes(self, key):
         """Size of a new plan of this shape: measured before for the shape, else
-        scaled from the plans of the same block size (25% margin), else unknown."""
+        scaled by points from the largest plan of the same block size (25%
+        margin; small plans carry more per-point overhead), else unknown."""
         if key in self.pools.known:
             return self.pools.known[key]
-        r = self.bytes_per_point.get(self.problems[key].n_b)
-        return None if r is None else 1.25 * r * self.points(key)
+        big = self.largest.get(self.problems[key].n_b)
+        return None if big is None else 1.25 * big[1] * self.points(key) / big[0]
 
     def _make(self, key):
         p = self.problems[key]
@@ -227,8 +228,8 @@ class GpuServer:
         u = self.torch.empty_like(f)
         uh = self.torch.empty(shape, dtype=self.dtype).pin_memory()
         nbytes = s.workspace_bytes() + 2 * f.numel() * f.element_size()
-        r = nbytes / self.points(key)
-        self.bytes_per_point[p.n_b] = max(r, self.bytes_per_point.get(p.n_b, 0.0))
+        if self.points(key) > self.largest.get(p.n_b, (0, 0))[0]:
+            self.largest[p.n_b] = (self.points(key), nbytes)
         return (s, f, u, uh), nbytes
 
     def _drop(self, handle):
@@ -257,8 +258,10 @@ class GpuServer:
         return True
 
     def warm(self, keys):
-        """One resident plan per shape, made before the stream starts."""
-        slots = [self.pools.acquire(k, 0.0, self.need_bytes(k)) for k in keys]
+        """One resident plan per shape, made before the stream starts (largest
+        first; each plan's size is measured, not estimated)."""
+        keys = sorted(keys, key=self.points, reverse=True)
+        slots = [self.pools.acquire(k, 0.0) for k in keys]
         for sl in slots:
             if sl is not None:
                 self.pools.release(sl, 0.0)
