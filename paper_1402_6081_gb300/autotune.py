@@ -21,10 +21,13 @@ from . import LGF_FP32
 
 _LOCK = threading.Lock()
 
+# interval_kernel 0 = the library's choice (persistent form where a level has
+# enough groups), 1 = one CTA per frequency chunk, 3 = paired groups, 4 =
+# persistent everywhere
 CANDIDATES = {
-    4: [{"fft_size_interval": 10, "interval_kernel": 1}],
-    8: [{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (1, 3)],
-    16: [{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (1, 3)],
+    4: [{"fft_size_interval": 10, "interval_kernel": k} for k in (0, 1)],
+    8: [{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (0, 1, 3, 4)],
+    16: [{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (0, 1, 4)],
 }
 
 
@@ -108,7 +111,7 @@ def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = 
             return dict(hit["options"])
     cands = CANDIDATES.get(n_b, [{}])
     if precision != LGF_FP32:
-        cands = [c for c in cands if c.get("interval_kernel", 1) == 1]
+        cands = [c for c in cands if c.get("interval_kernel", 1) in (0, 1)]
     timings = []
     for c in cands:
         try:
