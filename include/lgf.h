@@ -58,8 +58,21 @@ typedef enum {
 typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
 
 /* Arithmetic of the regularization / interpolation contractions (Eqs. alg_reg,
- * alg_interp).  NATIVE uses the plan precision on the CUDA cores. */
-typedef enum { LGF_INTERP_NATIVE = 0 } lgf_interp_mode;
+ * alg_interp).  NATIVE uses the plan precision on the CUDA cores.  The others
+ * (FP32 plans only) run each axis pass as a tensor-core GEMM (tcgen05.mma)
+ * with FP32 accumulation; the field between passes stays FP32 and only the
+ * MMA inputs (field values and weights) are rounded:
+ *   LGF_INTERP_BF16    BF16 inputs (8-bit significand)
+ *   LGF_INTERP_FP16    FP16 inputs (11-bit significand; magnitudes above
+ *                      65504 overflow: fields of order 1e4 or more need NATIVE)
+ *   LGF_INTERP_BF16X3  inputs split into three BF16 parts, six partial
+ *                      products: close to FP32 accuracy */
+typedef enum {
+    LGF_INTERP_NATIVE = 0,
+    LGF_INTERP_BF16 = 1,
+    LGF_INTERP_FP16 = 2,
+    LGF_INTERP_BF16X3 = 3
+} lgf_interp_mode;
 
 /*
  * lgf_plan_create - build the tree, lists, interpolation stencils and kernel
@@ -78,7 +91,9 @@ typedef enum { LGF_INTERP_NATIVE = 0 } lgf_interp_mode;
  *                 nodes are used per point, 1 <= n_max <= n_b + 1
  *   precision     LGF_FP32 or LGF_FP64 (FFTs, products and interpolation);
  *                 the LGF values and spectra are always generated in FP64
- *   interp_mode   LGF_INTERP_NATIVE
+ *   interp_mode   LGF_INTERP_NATIVE, or for FP32 plans LGF_INTERP_BF16,
+ *                 LGF_INTERP_FP16, LGF_INTERP_BF16X3 (LGF_ERR_UNSUPPORTED for
+ *                 FP64 plans)
  *   out           receives the plan
  *
  * Runs on the host plus uploads on the current device; synchronous.

@@ -18,6 +18,9 @@ LGF_OK = 0
 LGF_FP64 = 0
 LGF_FP32 = 1
 LGF_INTERP_NATIVE = 0
+LGF_INTERP_BF16 = 1
+LGF_INTERP_FP16 = 2
+LGF_INTERP_BF16X3 = 3
 
 _STATUS = {0: "LGF_OK", 1: "LGF_ERR_INVALID_ARG", 2: "LGF_ERR_UNSUPPORTED", 3: "LGF_ERR_OOM",
            4: "LGF_ERR_CUDA", 5: "LGF_ERR_TIMEOUT", 6: "LGF_ERR_BUDGET"}
@@ -314,11 +317,11 @@ class Solver:
 
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                 single_stream: int = 0, separate_level1: int = 0):
+                 single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
-        self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision,
+        self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision, interp_mode,
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
                                        interval_kernel=interval_kernel, single_stream=single_stream,
                                        separate_level1=separate_level1)

@@ -110,4 +110,11 @@ struct Launch {
                               T* u, const T* up, const T* W, int accumulate, const int* block, cudaStream_t st);
 };
 
+// Reg and Interp on the tensor cores for FP32 plans (interp_tc.cu); mode is
+// an lgf_interp_mode other than NATIVE, err the plan's device error flag.
+cudaError_t interp_tc(int mode, int n_b, const int* slot, const int* parent, int n_items, float* u, const float* up,
+                      const float* W, int accumulate, const int* block, int* err, cudaStream_t st);
+cudaError_t reg_tc(int mode, int n_b, const float* child_src, int child_is_block, const int* child_index,
+                   const int* parent_slot, int n_parents, float* dst, const float* W, int* err, cudaStream_t st);
+
 }  // namespace lgf

@@ -288,6 +288,7 @@ struct lgf_plan_s {
     int S0 = 0, SI = 0, Lmac = 0;
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     int single_stream = 0;
+    int interp_mode = LGF_INTERP_NATIVE;   // Reg/Interp arithmetic (FP32 plans: tensor-core modes)
     int* err = nullptr;                 // device flag: a bounded wait in a kernel ran out
     // levels 0 and 1 share the block grid and S0 = 2 n_b suffices for the
     // first n_b nodes of a level-1 interval: their products are summed into
@@ -823,14 +824,29 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if (!P->merged) LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
         if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
     }
+    // Interp of level l + 1 into the level-l items of D (see Launch::interp)
+    auto interp = [&](DevLevel& D, T* out, const T* up, int accumulate, const int* block, cudaStream_t s) {
+        if constexpr (sizeof(T) == 4) {
+            if (P->interp_mode != LGF_INTERP_NATIVE)
+                return interp_tc(P->interp_mode, nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block,
+                                 P->err, s);
+        }
+        return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block, s);
+    };
     // ---- levels >= 2 upward on s2: Reg from the level below, forward FFT
     auto up_part = [&]() -> lgf_status {
         for (int l = 2; l <= Lm; ++l) {
             DevLevel& D = lev[size_t(l)];
             const bool from_blocks = l == 2;
             e = timed(P, "reg", s2, [&] {
-                return Lc::reg(nb, P->n_max, from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft),
-                               from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg, static_cast<T*>(D.ft), W, s2);
+                const T* src = from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft);
+                if constexpr (sizeof(T) == 4) {
+                    if (P->interp_mode != LGF_INTERP_NATIVE)
+                        return reg_tc(P->interp_mode, nb, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
+                                      static_cast<T*>(D.ft), W, P->err, s2);
+                }
+                return Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
+                               static_cast<T*>(D.ft), W, s2);
             });
             if (e != cudaSuccess) return cuda_fail(e, "regularization");
             if (D.m2l) {
@@ -867,8 +883,8 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             }
             if (l < Lm) {
                 e = timed(P, "interp", s2, [&] {
-                    return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                                      static_cast<const T*>(lev[size_t(l) + 1].ut), W, 1, nullptr, s2);
+                    return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[size_t(l) + 1].ut), 1, nullptr,
+                                  s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interpolation");
             }
@@ -910,8 +926,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         LGF_CUDA(wait(s2, 3));
         DevLevel& D = lev[1];
         e = timed(P, "interp", s2, [&] {
-            return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, u, static_cast<const T*>(lev[2].ut), W, 1,
-                              D.int_block, s2);
+            return interp(D, u, static_cast<const T*>(lev[2].ut), 1, D.int_block, s2);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interpolation");
         LGF_CUDA(record(4, s2));
@@ -955,8 +970,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         // merged form: u~1 holds only the interpolated level-2 field (stored);
         // otherwise it already holds the level-1 products' field (added to)
         e = timed(P, "interp", st, [&] {
-            return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, static_cast<T*>(D.ut),
-                              static_cast<const T*>(lev[2].ut), W, P->merged ? 0 : 1, nullptr, st);
+            return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), P->merged ? 0 : 1, nullptr, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interpolation");
     }
@@ -1026,8 +1040,10 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: precision must be LGF_FP32 or LGF_FP64");
-    if (interp_mode != LGF_INTERP_NATIVE)
-        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: interp_mode must be LGF_INTERP_NATIVE");
+    if (interp_mode < LGF_INTERP_NATIVE || interp_mode > LGF_INTERP_BF16X3)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..3");
+    if (interp_mode != LGF_INTERP_NATIVE && precision != LGF_FP32)
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: reduced-precision interpolation modes need an FP32 plan");
     auto P = std::make_unique<lgf_plan_s>();
     cudaError_t e = cudaGetDevice(&P->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -1035,6 +1051,7 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     P->n_I = n_b + 1;
     P->n_max = interp_order + 1;
     P->prec = precision;
+    P->interp_mode = interp_mode;
     P->n_blocks = n_blocks;
     P->n_problems = n_problems;
     P->n_points = n_blocks * int64_t(n_b) * n_b * n_b;
