@@ -275,6 +275,53 @@ def batch_run(torch, lgfm, steps: int, warmup: int, flush):
     return out
 
 
+def irregular_run(torch, lgfm, steps: int, flush):
+    """The 512^3 irregular domain (12 tori, 7252 blocks of 16^3, 22% occupancy,
+    5 levels, order 8): points/s and the error of each interpolation mode
+    against the plain FP64 form on the same GPU (which the parity tests tie to
+    the FP64 oracle at 1e-12 on the other configs)."""
+    p = W.tori_irregular(2)
+    stream = torch.cuda.Stream()
+    modes = {"fp32": lgfm.LGF_INTERP_NATIVE, "bf16": lgfm.LGF_INTERP_BF16, "fp16": lgfm.LGF_INTERP_FP16,
+             "bf16x3": lgfm.LGF_INTERP_BF16X3}
+
+    def run(prec, mode, k):
+        dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, interp_mode=mode)
+        f = torch.from_numpy(p.f).to(dt).cuda()
+        u = torch.empty_like(f)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                s(f, u, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                flush.fill_(1.0)
+                a.record(stream)
+                s(f, u, stream)
+                b.record(stream)
+        lgfm.lgf_plan_sync(s.plan)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        out = u.double().cpu().numpy()
+        s.close()
+        return ms, out
+
+    ms64, u64 = run(lgfm.LGF_FP64, lgfm.LGF_INTERP_NATIVE, 3)
+    scale = float(np.abs(u64).max())
+    res = {"fp64": {"value": p.n_points / (ms64 * 1e-3), "ms_per_step": ms64}}
+    for name, mode in modes.items():
+        ms, u = run(lgfm.LGF_FP32, mode, steps)
+        res[name] = {"value": p.n_points / (ms * 1e-3), "ms_per_step": ms,
+                     "rel_err_vs_fp64": float(np.abs(u - u64).max()) / scale}
+    out = dict(res["fp32"])
+    out.update({"unit": "points/s", "modes": res,
+                "config": {"workload": "tori_irregular_512", "points": p.n_points, "blocks": len(p.blocks),
+                           "levels": p.n_levels, "interp_order": p.order,
+                           "l2": "flushed: 256 MiB write before every timed step"}})
+    return out
+
+
 def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
     """Poisson arrivals (200/s, seed 1) of torus solves with point counts
     log-uniform in 2^12..2^24, admitted under a 120 GB HBM budget, FP32 form
@@ -334,6 +381,7 @@ def main():
     ap.add_argument("--interval-kernel", type=int, default=0, help="interval product kernel variant (0 = default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-solve batched workload")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson-arrival serving workload")
+    ap.add_argument("--no-irregular", action="store_true", help="skip the 512^3 irregular-domain workload")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -479,7 +527,13 @@ def main():
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
                 "algorithmic": "8 flop x " + work[dom_name][1],
                 "ms_in_step": dom_ms, "ms_isolated": iso_ms,
-                "frac_isolated": flops / (iso_ms * 1e-3) / 1e12 / peak_tf}
+                "frac_isolated": flops / (iso_ms * 1e-3) / 1e12 / peak_tf,
+                # the streaming model (every complex MAC reads a source and a
+                # kernel value, 16 B in FP32): what HBM would have to deliver
+                # without on-chip reuse, against the measured copy bandwidth
+                "streamed_model_gbs": 16.0 * work[dom_name][0] / (dom_ms * 1e-3) / 1e9,
+                "streamed_model_frac_of_hbm": 16.0 * work[dom_name][0] / (dom_ms * 1e-3) / 1e9
+                / float(pk.get("hbm_gbs", 6800.0))}
     else:
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": None, "peak": pk.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}
@@ -518,6 +572,11 @@ def main():
             out["batch"] = batch_run(torch, lgfm, max(3, min(200, args.steps // 10)), 3, flush)
         except Exception as exc:       # reported in the line, the headline stands
             out["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if world == 1 and not args.no_irregular:
+        try:
+            out["irregular"] = irregular_run(torch, lgfm, max(3, min(50, args.steps // 40)), flush)
+        except Exception as exc:
+            out["irregular"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and not args.no_serve:
         try:
             out["serve"] = serve_run(torch, lgfm)
