@@ -1,0 +1,67 @@
+"""Truncation error of the method against exact manufactured solutions
+(Sec. 4.1) on cube, sphere and spherical-shell active grids of the same
+physical size, for interval sizes n_I = 5, 9, 17 at a fixed interpolation
+order: the paper's error experiment (Sec. 4, error against n_I at fixed n_max).
+The FP64 path is used, so the error is the method's own; at fixed n_max it
+falls as n_I grows (finer intervals relative to the kernel's smoothness).
+Rates (points/s, FP32 and FP64) are recorded with the errors."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1402_6081_gb300 as lgfm
+import workloads as W
+from oracle import fmm
+from paper_1402_6081_gb300 import build as lgf_build
+from conftest import record_error
+
+pytestmark = pytest.mark.gpu
+
+DIAMETER = 96
+ORDER = 4           # n_max = 5 <= n_I for every block size
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lgf_build.build()
+    lgfm.library()
+
+
+def _solve(m, prec, reps=3):
+    dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+    s = lgfm.Solver(m.blocks, m.n_b, m.n_levels, m.order, prec)
+    f = torch.from_numpy(m.f).to(dt).cuda()
+    u = torch.empty_like(f)
+    s(f, u)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        s(f, u)
+    b.record()
+    b.synchronize()
+    rate = m.n_points * reps / (a.elapsed_time(b) * 1e-3)
+    out = u.double().cpu().numpy()
+    s.close()
+    return out, rate
+
+
+@pytest.mark.parametrize("shape", ["box", "sphere", "shell"])
+def test_error_falls_with_interval_size(shape):
+    errs = []
+    for n_b in (4, 8, 16):
+        blocks = W.shape_blocks(shape, DIAMETER, n_b)
+        L = W.levels_for(int(np.ceil(DIAMETER / n_b)))
+        m = W.manufactured(blocks, n_b, L, ORDER, seed=11)
+        u64, r64 = _solve(m, lgfm.LGF_FP64)
+        u32, r32 = _solve(m, lgfm.LGF_FP32)
+        e64 = fmm.rel_linf(u64, m.u_exact)
+        e32 = fmm.rel_linf(u32, m.u_exact)
+        record_error(f"sweep_{shape}_nI{n_b + 1}", fp64_vs_exact=e64, fp32_vs_exact=e32, points=m.n_points,
+                     fp64_points_per_s=r64, fp32_points_per_s=r32)
+        print(f"{shape} n_I {n_b + 1}: fp64 err {e64:.3e} fp32 err {e32:.3e} "
+              f"rate fp32 {r32:.3e} fp64 {r64:.3e} points {m.n_points}")
+        errs.append(e64)
+    assert errs[0] > errs[1] > errs[2], errs

@@ -158,6 +158,24 @@ def tori_irregular(seed: int = 2, nb: int = 32, n_b: int = 16, n_tori: int = 12,
                    f"tori_irregular_{side}")
 
 
+def shape_blocks(shape: str, diameter: int, n_b: int) -> np.ndarray:
+    """Active blocks of a cube, a sphere or a spherical shell of the given
+    diameter in grid points (the paper's error and rate experiments, Sec. 4):
+    a block is active when its centre lies in the region; the shell keeps
+    radii between half and all of the outer radius."""
+    nb = max(1, int(math.ceil(diameter / n_b)))
+    blocks = full_box_blocks(nb)
+    if shape == "box":
+        return blocks
+    c = (blocks + 0.5) * n_b - nb * n_b / 2.0
+    r = np.sqrt((c ** 2).sum(axis=1))
+    R = diameter / 2.0
+    keep = r <= R if shape == "sphere" else (r <= R) & (r >= 0.5 * R)
+    if shape not in ("sphere", "shell"):
+        raise ValueError(shape)
+    return blocks[keep].copy()
+
+
 def manufactured(blocks: np.ndarray, n_b: int, n_levels: int, order: int,
                  seed: int = 0) -> Problem:
     """Random manufactured solution of Sec. 4.1: u ~ U(-1,1) on the active grid,
