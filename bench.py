@@ -379,6 +379,8 @@ def main():
                     help="FFT length per axis at the interval levels (0 = library default)")
     ap.add_argument("--near-kernel", type=int, default=0, help="level-0 product kernel variant (0 = default)")
     ap.add_argument("--interval-kernel", type=int, default=0, help="interval product kernel variant (0 = default)")
+    ap.add_argument("--free-sms", type=int, default=0,
+                    help="SMs left to levels >= 2 beside the persistent products (-1: split schedule, 0: default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-solve batched workload")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson-arrival serving workload")
     ap.add_argument("--no-irregular", action="store_true", help="skip the 512^3 irregular-domain workload")
@@ -419,7 +421,7 @@ def main():
     def make(prec):
         dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
         s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, fft_size_interval=args.fft_size,
-                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel)
+                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel, free_sms=args.free_sms)
         f = torch.from_numpy(p.f).to(dt).cuda()
         u = torch.empty_like(f)
         return s, f, u
@@ -478,7 +480,8 @@ def main():
     # the same kernels once more with every launch on one stream, so the
     # dominant kernel is also timed without other chains sharing the SMs
     s_iso = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, fft_size_interval=args.fft_size,
-                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel, single_stream=1)
+                        near_kernel=args.near_kernel, interval_kernel=args.interval_kernel, single_stream=1,
+                        free_sms=args.free_sms)
     k_iso = max(3, min(100, args.steps // 10))
     timed_steps(s_iso, f32, u32, k_iso, 3, timing_capacity=k_iso * 16)
     kt_iso, _ = lgfm.lgf_plan_timings(s_iso.plan)
@@ -512,7 +515,11 @@ def main():
     S0, SI = st["fft_size_level0"], st["fft_size_interval"]
     nw = {0: st["nw"][0], 1: st["nw"][1]}
     # useful complex products per launch of each product kernel
+    upper = [(l, st["pairs"][l], st["nw"][l]) for l in range(2, p.n_levels) if st["nw"][l]]
     work = {"mac_level0": (pairs[0] * nw[0], f"{pairs[0]} near pairs x {nw[0]} frequencies"),
+            "mac_all_levels": ((pairs[0] + pairs[1]) * nw[0] + sum(a * b for _, a, b in upper),
+                               f"({pairs[0]} near + {pairs[1]} level-1 interaction pairs) x {nw[0]} frequencies"
+                               + "".join(f" + {a} level-{l} pairs x {b}" for l, a, b in upper)),
             "mac_level01": ((pairs[0] + pairs[1]) * nw[0],
                             f"({pairs[0]} near + {pairs[1]} level-1 interaction pairs) x {nw[0]} frequencies"),
             "mac_interval_l1": (pairs[1] * nw[1], f"{pairs[1]} interaction pairs x {nw[1]} frequencies")}

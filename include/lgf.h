@@ -135,6 +135,11 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      the parent neighbourhood (343 kernel offsets) and one
  *                      inverse FFT.  1: separate level-1 transforms of length
  *                      S_I, as the level interactions of Sec. 3.1 are listed.
+ *   free_sms           schedule of the persistent products (interval_kernel
+ *                      form 4): -1 = they take every SM and levels >= 2 run
+ *                      before and after them; k > 0 = they take all but k SMs
+ *                      and levels >= 2 run beside them on the rest; 0 = the
+ *                      library's choice
  * All variants compute the same sums (Eq. alg_mult); they differ only in
  * scheduling.
  */
@@ -144,7 +149,8 @@ typedef struct {
     int32_t interval_kernel;
     int32_t single_stream;
     int32_t separate_level1;
-    int32_t reserved[11];
+    int32_t free_sms;
+    int32_t reserved[10];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */

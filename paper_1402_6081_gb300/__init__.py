@@ -118,7 +118,8 @@ MAX_LEVELS = 24
 class lgf_plan_options(ctypes.Structure):
     _fields_ = [("fft_size_interval", ctypes.c_int32), ("near_kernel", ctypes.c_int32),
                 ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
-                ("separate_level1", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("separate_level1", ctypes.c_int32), ("free_sms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -146,10 +147,11 @@ def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
 def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
                        fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                       single_stream: int = 0, separate_level1: int = 0) -> int:
+                       single_stream: int = 0, separate_level1: int = 0, free_sms: int = 0) -> int:
     """lgf_plan_create with tuning options (0 = default)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
     opts = lgf_plan_options()
+    opts.free_sms = free_sms
     opts.fft_size_interval = fft_size_interval
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
@@ -162,8 +164,10 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
     return out.value
 
 
-def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0):
+def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0,
+             free_sms=0):
     opts = lgf_plan_options()
+    opts.free_sms = free_sms
     opts.fft_size_interval = fft_size_interval
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
@@ -317,14 +321,15 @@ class Solver:
 
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                 single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE):
+                 single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE,
+                 free_sms: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
         self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision, interp_mode,
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
                                        interval_kernel=interval_kernel, single_stream=single_stream,
-                                       separate_level1=separate_level1)
+                                       separate_level1=separate_level1, free_sms=free_sms)
 
     @property
     def dtype(self):

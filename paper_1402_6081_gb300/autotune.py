@@ -22,12 +22,14 @@ from . import LGF_FP32
 _LOCK = threading.Lock()
 
 # interval_kernel 0 = the library's choice (persistent form where a level has
-# enough groups), 1 = one CTA per frequency chunk, 3 = paired groups, 4 =
-# persistent everywhere
+# enough groups), 1 = one CTA per frequency chunk, 3 = paired groups;
+# free_sms: SMs left to levels >= 2 beside the persistent products (-1: none)
 CANDIDATES = {
     4: [{"fft_size_interval": 10, "interval_kernel": k} for k in (0, 1)],
-    8: [{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (0, 1, 3, 4)],
-    16: [{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (0, 1, 4)],
+    8: ([{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (0, 1, 3)]
+        + [{"fft_size_interval": 17, "interval_kernel": 0, "free_sms": f} for f in (-1, 8, 32)]),
+    16: ([{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (0, 1)]
+         + [{"fft_size_interval": 33, "interval_kernel": 0, "free_sms": f} for f in (-1, 8, 32)]),
 }
 
 

@@ -275,7 +275,7 @@ struct DevLevel {
     int* int_block = nullptr;       // level 1: the block of each item (output into the blocks)
     int n_int = 0;
     std::shared_ptr<SpecEntry> kh;
-    PersistPlan pp;                 // work lists of the persistent products (FP32)
+    PersistPlan pp;                 // work lists and CTA ranges of the persistent products (FP32)
 };
 
 }  // namespace lgf
@@ -290,6 +290,9 @@ struct lgf_plan_s {
     int single_stream = 0;
     int interp_mode = LGF_INTERP_NATIVE;   // Reg/Interp arithmetic (FP32 plans: tensor-core modes)
     int* err = nullptr;                 // device flag: a bounded wait in a kernel ran out
+    // SMs left to the levels >= 2 chain beside the persistent level-0 products
+    // (-1: none; the chain then runs before and after them)
+    int free_sms = 0;
     // levels 0 and 1 share the block grid and S0 = 2 n_b suffices for the
     // first n_b nodes of a level-1 interval: their products are summed into
     // one spectrum per block (one inverse FFT, no level-1 transforms)
@@ -408,12 +411,19 @@ static bool uses_persist(const lgf_plan_s* P, int l) {
     if (P->prec != LGF_FP32) return false;
     if (P->interval_kernel != 0 && P->interval_kernel != 4) return false;
     if (l == 0 && !P->merged) return false;
+    // beside shared-SM level-0 products, the other levels keep the
+    // one-CTA-per-chunk form, which fits on the SMs left to them
+    if (l >= 2 && P->free_sms > 0 && P->Lmac >= 2 && P->merged) return false;
     return P->interval_kernel == 4 || P->lev[size_t(l)].n_groups >= 48;
 }
 
-// Work lists of the persistent kernel for one level (see PersistPlan).
+// Work lists of the persistent kernel for one level (see PersistPlan); the
+// level's units (frequency chunk of 32, group position) are split at group
+// boundaries into one range per CTA of about equal work (a unit weighs its
+// pairs plus one for the group's set-up and stores).  The launch has one CTA
+// per SM, less `free` SMs left to other kernels.
 static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<int>& gn, const std::vector<int>& ord,
-                                int S, bool include_self) {
+                                int S, bool include_self, int free) {
     const int G = D.n_groups;
     std::vector<PairSrc> pairs;
     std::vector<int> start(size_t(G) + 1, 0);
@@ -429,17 +439,16 @@ static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<in
     }
     int n_sm = 0;
     LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
-    const long long chunks = nws_of(S) / 32, n_cta = std::max(1, n_sm);
-    // unit weight: its pairs plus one for the group's set-up and stores
+    const long long chunks = nws_of(S) / 32, n_cta = std::max(1, n_sm - std::max(0, free));
     std::vector<long long> pre(size_t(G) + 1, 0);
-    for (int pos = 0; pos < G; ++pos) pre[size_t(pos) + 1] = pre[size_t(pos)] + (start[size_t(pos) + 1] - start[size_t(pos)]) + 1;
+    for (int pos = 0; pos < G; ++pos)
+        pre[size_t(pos) + 1] = pre[size_t(pos)] + (start[size_t(pos) + 1] - start[size_t(pos)]) + 1;
     const long long Wg = pre[size_t(G)], Wt = Wg * chunks;
     std::vector<long long> cut(size_t(n_cta) + 1);
     for (long long b = 0; b <= n_cta; ++b) {
         const long long T = (Wt * b) / n_cta;
         const long long c = std::min(T / Wg, chunks);
-        const long long rem = T - c * Wg;
-        const long long pos = std::lower_bound(pre.begin(), pre.end(), rem) - pre.begin();
+        const long long pos = std::lower_bound(pre.begin(), pre.end(), T - c * Wg) - pre.begin();
         cut[size_t(b)] = std::min(c * G + std::min<long long>(pos, G), chunks * G);
     }
     cut[0] = 0;
@@ -691,7 +700,9 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                 }
                 std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cnt[size_t(a)] > cnt[size_t(b)]; });
                 if ((s = upload(P, ord, &D.order)) != LGF_OK) return s;
-                if (uses_persist(P, l) && (s = build_persist(P, D, gn, ord, S, l == 0)) != LGF_OK) return s;
+                // with a levels >= 2 chain beside the level-0 products, leave SMs for it
+                const int free = l == 0 && Lmac >= 2 ? P->free_sms : 0;
+                if (uses_persist(P, l) && (s = build_persist(P, D, gn, ord, S, l == 0, free)) != LGF_OK) return s;
             }
             D.n_r2c = int(items.size());
             if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
@@ -815,7 +826,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     // inverse FFT, and the level-2 field is finally interpolated straight into
     // the blocks.  Otherwise levels >= 2 run beside the level-0 products and
     // their level-1 field is added by the level-0 inverse FFT.
-    const bool split = Lm >= 2 && uses_persist(P, 0);
+    const bool split = Lm >= 2 && uses_persist(P, 0) && P->free_sms < 0;
     auto record = [&](int k, cudaStream_t s) { return conc ? cudaEventRecord(P->join[k], s) : cudaSuccess; };
     auto wait = [&](cudaStream_t s, int k) { return conc ? cudaStreamWaitEvent(s, P->join[k], 0) : cudaSuccess; };
     // fork: the other chains start after all prior work on the caller's stream
@@ -1071,7 +1082,10 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         P->interval_kernel = opts->interval_kernel;
         P->single_stream = opts->single_stream != 0;
         P->merged = opts->separate_level1 == 0;
+        if (opts->free_sms < -1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: free_sms must be >= -1");
+        P->free_sms = opts->free_sms;
     }
+    if (P->free_sms == 0) P->free_sms = 16;
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
     std::vector<HostPlan> hp(static_cast<size_t>(n_problems));

@@ -233,6 +233,20 @@ def test_timing_api_counts_launches():
     assert t["mac_level01"][1] == 2 and t["mac_level01"][0] > 0
     assert sum(c for _, c in t.values()) == 16
     s.close()
+    for free in (-1, 24):
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, free_sms=free)
+        lgfm.lgf_plan_set_timing(s.plan, 64)
+        s(f)
+        t, per = lgfm.lgf_plan_timings(s.plan)
+        assert per == 8 and t["mac_level01"][1] == 1
+        s.close()
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, interval_kernel=1)
+    lgfm.lgf_plan_set_timing(s.plan, 64)
+    s(f)
+    t, per = lgfm.lgf_plan_timings(s.plan)
+    # one CTA per frequency chunk: r2c x2, products x2, reg, c2r x2, interp
+    assert per == 8 and t["mac_level01"][1] == 1 and t["mac_interval_l2plus"][1] == 1
+    s.close()
     s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, separate_level1=1)
     lgfm.lgf_plan_set_timing(s.plan, 64)
     s(f)
