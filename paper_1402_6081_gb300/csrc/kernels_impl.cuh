@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "fft_device.cuh"
 #include "lgf_internal.h"
 
@@ -327,6 +329,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// 2D tensor-map copy of one box at element coordinates (x, y) into this
+// CTA's shared memory (128-byte aligned), completion counted on bar
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// A chunk of 343 coefficient rows arrives as two boxes of kTmaRows rows
+// (the second box's last row lies past the table and is zero-filled).
+constexpr int kTmaRows = 172;
+
 constexpr int kMacWarps = 12;
 
 // One warp's walk over the (group, neighbour) pairs it owns: groups
@@ -436,15 +452,34 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
                                                                    cx<T>* __restrict__ uh,
                                                                    const int* __restrict__ gnbr,
                                                                    const int* __restrict__ order, int n_groups,
-                                                                   int groups_per_cta, int include_self) {
+                                                                   int groups_per_cta, int include_self,
+                                                                   const __grid_constant__ CUtensorMap tmap,
+                                                                   int use_tma, int* __restrict__ err) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [2 kTmaRows][32]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(cx<T>) * 2 * kTmaRows * 32);
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    stage_coefficients<T, NW, NWS, 32 * kMacWarps>(sk, kh, w0, tid);
-    __syncthreads();
+    if (use_tma) {
+        // the chunk's rows as two tensor boxes (x in reals: 2 per complex)
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbar_expect_tx(bar, unsigned(sizeof(cx<T>) * 2 * kTmaRows * 32));
+            tma_2d(sk, &tmap, int(2 * w0), 0, bar);
+            tma_2d(sk + kTmaRows * 32, &tmap, int(2 * w0), kTmaRows, bar);
+        }
+        __syncthreads();
+        if (!mbar_wait(bar, 0)) {
+            if (tid == 0) atomicExch(err, 1);
+            return;
+        }
+    } else {
+        stage_coefficients<T, NW, NWS, 32 * kMacWarps>(sk, kh, w0, tid);
+        __syncthreads();
+    }
     const int g0 = blockIdx.x * groups_per_cta;
     const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
@@ -875,18 +910,19 @@ __device__ __forceinline__ void persist_block(cx<float> (&acc)[8], const cx<floa
         }
 }
 
-constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
+constexpr unsigned kPersistBuf = 2u * kTmaRows * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
 constexpr size_t kPersistSmem = 2 * size_t(kPersistBuf) + 64;
 
 template <int S>
 __global__ void __launch_bounds__(32 * kPersistWarps, 1)
     k_mac_persist(const cx<float>* __restrict__ fh, const cx<float>* __restrict__ kh, cx<float>* __restrict__ uh,
                   const PairSrc* __restrict__ pairs, const int* __restrict__ start, const int* __restrict__ order,
-                  const long long* __restrict__ cta_units, int n_groups, int* __restrict__ err) {
+                  const long long* __restrict__ cta_units, int n_groups, int* __restrict__ err,
+                  const __grid_constant__ CUtensorMap tmap, int use_tma) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][343][32]
+    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][2 kTmaRows][32]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * kPersistBuf);   // [2]
     int* ctr = reinterpret_cast<int*>(full + 2);                             // [2] next position
     int* done = ctr + 2;                                                     // [2] warps finished
@@ -905,8 +941,17 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
     // one warp issues the 343 row copies of chunk c (256 bytes each)
     auto fill = [&](long long c) {
         const int b = int((c - c0) & 1);
-        cx<float>* dst = buf + b * (343 * 32);
-        if (lane == 0) mbar_expect_tx(&full[b], kPersistBuf);
+        cx<float>* dst = buf + b * (2 * kTmaRows * 32);
+        if (use_tma) {
+            // two tensor boxes (x in reals: 2 per complex)
+            if (lane == 0) {
+                mbar_expect_tx(&full[b], kPersistBuf);
+                tma_2d(dst, &tmap, int(c * 64), 0, &full[b]);
+                tma_2d(dst + kTmaRows * 32, &tmap, int(c * 64), kTmaRows, &full[b]);
+            }
+            return;
+        }
+        if (lane == 0) mbar_expect_tx(&full[b], 343u * 256u);
         __syncwarp();
         const cx<float>* src = kh + c * 32;
         for (int d = lane; d < 343; d += 32) bulk_g2s(dst + d * 32, src + int64_t(d) * NWS, 256u, &full[b]);
@@ -921,7 +966,7 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
             if (lane == 0) atomicExch(err, 1);
             return;
         }
-        const cx<float>* sk = buf + b * (343 * 32) + lane;
+        const cx<float>* sk = buf + b * (2 * kTmaRows * 32) + lane;
         const int pb = c == c0 ? int(u0 % n_groups) : 0;
         const int pe = c == c1 ? int((u1 - 1) % n_groups) + 1 : n_groups;
         const int64_t w = c * 32 + lane;
@@ -1360,7 +1405,8 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
 
 template <typename T, int S>
 static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                       int n_groups, int variant, int include_self, cudaStream_t st) {
+                                       int n_groups, int variant, int include_self, const CUtensorMap* tmap, int* err,
+                                       cudaStream_t st) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     const auto* f = static_cast<const dev::cx<T>*>(fh);
     const auto* k = static_cast<const dev::cx<T>*>(kh);
@@ -1400,7 +1446,7 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
         kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
         return cudaGetLastError();
     }
-    const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
+    const size_t smem = sizeof(dev::cx<T>) * 2 * dev::kTmaRows * 32 + 16;
     auto kern = dev::k_mac_interval<T, S>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -1408,15 +1454,20 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
     const int64_t nchunks = (NW + 31) / 32;
     const int per = groups_per_cta(dev::kMacWarps, sizeof(T) == 4 ? 2 : 1, nchunks);
     dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
-    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self);
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if (tmap) map = *tmap;
+    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self, map, tmap ? 1 : 0, err);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                    int n_groups, int S, int variant, int include_self, cudaStream_t st) {
-#define LGF_MACI(SS) \
-    case SS: return launch_mac_interval<T, SS>(fh, kh, uh, gnbr, order, n_groups, variant, include_self, st);
+                                    int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
+                                    int* err, cudaStream_t st) {
+#define LGF_MACI(SS)                                                                                            \
+    case SS:                                                                                                    \
+        return launch_mac_interval<T, SS>(fh, kh, uh, gnbr, order, n_groups, variant, include_self, tmap, err, st);
     switch (S) {
         LGF_MACI(8) LGF_MACI(10) LGF_MACI(16) LGF_MACI(17) LGF_MACI(18) LGF_MACI(32) LGF_MACI(33) LGF_MACI(34)
         LGF_MACI(36)
@@ -1432,9 +1483,13 @@ static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::kPersistSmem));
     if (e != cudaSuccess) return e;
     if (pp.n_groups == 0 || pp.n_cta == 0) return cudaSuccess;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if (pp.tmap) map = *pp.tmap;
     kern<<<pp.n_cta, 32 * dev::kPersistWarps, dev::kPersistSmem, st>>>(
         static_cast<const dev::cx<float>*>(fh), static_cast<const dev::cx<float>*>(kh),
-        static_cast<dev::cx<float>*>(uh), pp.pairs, pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err);
+        static_cast<dev::cx<float>*>(uh), pp.pairs, pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err, map,
+        pp.tmap ? 1 : 0);
     return cudaGetLastError();
 }
 

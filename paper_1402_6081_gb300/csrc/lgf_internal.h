@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap (a plain struct; no driver call is linked)
 #include <cuda_runtime_api.h>
 
 #include "../../include/lgf.h"
@@ -69,6 +70,7 @@ struct C2RItem { int src; int dst; int aux; };
 // equal work; err is set when a wait in the kernel runs out.
 struct PairSrc { int src; int centre; };
 struct PersistPlan {
+    const CUtensorMap* tmap = nullptr;   // the level's kernel table as a 2D tensor (rows x 2 NWS reals)
     const PairSrc* pairs = nullptr;
     const int* start = nullptr;          // n_groups + 1 offsets into pairs
     const int* order = nullptr;          // group id per position
@@ -94,8 +96,11 @@ struct Launch {
                                   int n_groups, int S, int variant, cudaStream_t st);
     // order: the groups in work order (descending neighbour count);
     // include_self: the group's own block is a source (merged levels 0 and 1)
+    // tmap: the kernel table as a 2D tensor for TMA loads of the coefficient
+    // chunk (nullptr: plain loads); err: device flag for a wait that ran out
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
-                                    int n_groups, int S, int variant, int include_self, cudaStream_t st);
+                                    int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
+                                    int* err, cudaStream_t st);
     // The same products as mac_interval from a persistent kernel (one CTA per
     // SM) that stages the coefficient chunks with bulk copies; FP32 only.
     static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,

@@ -2,6 +2,7 @@
 // interpolation stencils of Sec. 2.5, the kernel spectra of Step 0 (Eq.
 // precomp), device workspace, and the launch sequence of Steps 1-3.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -99,6 +100,10 @@ struct SpecEntry {
     int device = 0;
     void* ptr = nullptr;
     size_t bytes = 0;
+    // the table as a 2D tensor (rows x 2 NWS reals) for TMA loads of
+    // coefficient chunks; valid when has_tmap
+    alignas(64) CUtensorMap tmap;
+    bool has_tmap = false;
     ~SpecEntry() {
         if (ptr) {
             int cur = 0;
@@ -145,6 +150,37 @@ void kernel_spectrum(int n_b, int n, int h, int S, const int d[3], const double*
     fft_lines(C.data(), S, S * NX, S * NX, 1, -1);
     const double inv = 1.0 / (double(S) * S * S);
     for (size_t i = 0; i < C.size(); ++i) outw[i] = C[i] * inv;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr when unavailable
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// rows x NWS complex values viewed as rows x 2 NWS reals; boxes of 32
+// complex values (64 reals) by 172 rows
+static bool encode_table_map(SpecEntry& e, int rows, int64_t nws, int prec) {
+    auto enc = tensor_map_encoder();
+    if (!enc || rows < 172) return false;
+    const bool f64 = prec == LGF_FP64;
+    const cuuint64_t dims[2] = {cuuint64_t(2 * nws), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(2 * nws) * (f64 ? 8 : 4)};
+    const cuuint32_t box[2] = {64, 172};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&e.tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, e.ptr,
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 static std::mutex g_spec_mu;
@@ -213,6 +249,7 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
         ce = cudaMemcpy(e->ptr, f.data(), e->bytes, cudaMemcpyHostToDevice);
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "spectra upload");
+    e->has_tmap = nd == 343 && encode_table_map(*e, nd, NWS, prec);
     g_spec_cache[key] = e;
     out = e;
     return ok();
@@ -407,13 +444,18 @@ struct HostPlan {
 // when it carries the merged level-0/level-1 products.  Its 24 warps share the
 // groups of one frequency chunk, so by default a level needs at least 48
 // groups (fewer leave warps idle; the one-CTA-per-chunk form is faster there).
+static bool uses_persist(const lgf_plan_s* P, int l);
+// The level-0 products leave free_sms SMs to a levels >= 2 chain beside them.
+static bool shares_sms(const lgf_plan_s* P) {
+    return P->free_sms > 0 && P->Lmac >= 2 && P->merged && uses_persist(P, 0);
+}
 static bool uses_persist(const lgf_plan_s* P, int l) {
     if (P->prec != LGF_FP32) return false;
     if (P->interval_kernel != 0 && P->interval_kernel != 4) return false;
     if (l == 0 && !P->merged) return false;
-    // beside shared-SM level-0 products, the other levels keep the
+    // beside shared-SM level-0 products, levels >= 2 keep the
     // one-CTA-per-chunk form, which fits on the SMs left to them
-    if (l >= 2 && P->free_sms > 0 && P->Lmac >= 2 && P->merged) return false;
+    if (l >= 2 && shares_sms(P)) return false;
     return P->interval_kernel == 4 || P->lev[size_t(l)].n_groups >= 48;
 }
 
@@ -700,8 +742,10 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                 }
                 std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cnt[size_t(a)] > cnt[size_t(b)]; });
                 if ((s = upload(P, ord, &D.order)) != LGF_OK) return s;
-                // with a levels >= 2 chain beside the level-0 products, leave SMs for it
-                const int free = l == 0 && Lmac >= 2 ? P->free_sms : 0;
+                // with a levels >= 2 chain beside the level-0 products, level 0
+                // leaves free_sms SMs to it
+                int free = 0;
+                if (l == 0 && Lmac >= 2) free = std::max(0, P->free_sms);
                 if (uses_persist(P, l) && (s = build_persist(P, D, gn, ord, S, l == 0, free)) != LGF_OK) return s;
             }
             D.n_r2c = int(items.size());
@@ -709,6 +753,7 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             const int h = l == 0 ? 1 : (1 << (l - 1));
             const int kind = l == 0 ? (P->merged ? kBlock : kNear) : kInterval;
             if ((s = get_spectra(P->device, nb, S, h, kind, P->prec, D.kh)) != LGF_OK) return s;
+            D.pp.tmap = D.kh->has_tmap ? &D.kh->tmap : nullptr;
         }
         if (l >= 1 && !(l == 1 && P->merged && Lmac < 2)) {
             if ((s = dalloc(P, slots * n3 * elem, &D.ut, true)) != LGF_OK) return s;
@@ -788,6 +833,9 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
     }
     return ok();
 }
+
+// A level's kernel table as a tensor map, when TMA loads are available for it
+static const CUtensorMap* table_map(const DevLevel& D) { return D.kh && D.kh->has_tmap ? &D.kh->tmap : nullptr; }
 
 // Runs one launch; with timing enabled, brackets it by an event pair on `st`.
 template <typename F>
@@ -877,7 +925,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "mac_interval_l2plus", s2, [&] {
                 if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s2);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
-                                        0, s2);
+                                        0, table_map(D), P->err, s2);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
         }
@@ -915,7 +963,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         e = timed(P, "mac_level01", st, [&] {
             if (uses_persist(P, 0)) return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, st);
             return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
-                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, st);
+                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, table_map(lev[0]), P->err, st);
         });
     } else {
         e = timed(P, "mac_level0", st, [&] {
@@ -954,7 +1002,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "mac_interval_l1", s1, [&] {
                 if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s1);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
-                                        0, s1);
+                                        0, table_map(D), P->err, s1);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
             e = timed(P, "c2r_interval", s1, [&] {
@@ -967,23 +1015,32 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         }
         LGF_CUDA(record(0, s1));
     }
-    // ---- levels >= 2 on s2 beside the products
+    // ---- levels >= 2 on s2 beside the products; in the merged form u~1
+    // holds only the interpolated level-2 field, stored at the chain's end
     if (Lm >= 2) {
         if ((r = up_part()) != LGF_OK) return r;
         if ((r = down_part()) != LGF_OK) return r;
+        if (P->merged) {
+            DevLevel& D = lev[1];
+            e = timed(P, "interp", s2, [&] {
+                return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 0, nullptr, s2);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+        }
         LGF_CUDA(record(1, s2));
     }
-    // ---- join, interpolate level 2 into level 1, and the level-0 output
+    // ---- join; in the separate form interpolate level 2 into the level-1
+    // products' field (added to); then the level-0 output
     if (Lm >= 1 && !P->merged) LGF_CUDA(wait(st, 0));
     if (Lm >= 2) {
         LGF_CUDA(wait(st, 1));
-        DevLevel& D = lev[1];
-        // merged form: u~1 holds only the interpolated level-2 field (stored);
-        // otherwise it already holds the level-1 products' field (added to)
-        e = timed(P, "interp", st, [&] {
-            return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), P->merged ? 0 : 1, nullptr, st);
-        });
-        if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+        if (!P->merged) {
+            DevLevel& D = lev[1];
+            e = timed(P, "interp", st, [&] {
+                return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 1, nullptr, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "interpolation");
+        }
     }
     const bool has_ut1 = P->merged ? Lm >= 2 : Lm >= 1;
     const T* add = has_ut1 ? static_cast<const T*>(lev[1].ut) : nullptr;
@@ -1085,7 +1142,7 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         if (opts->free_sms < -1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: free_sms must be >= -1");
         P->free_sms = opts->free_sms;
     }
-    if (P->free_sms == 0) P->free_sms = 16;
+    if (P->free_sms == 0) P->free_sms = 24;
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
     std::vector<HostPlan> hp(static_cast<size_t>(n_problems));
