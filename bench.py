@@ -534,6 +534,10 @@ def main():
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
                 "algorithmic": "8 flop x " + work[dom_name][1],
                 "ms_in_step": dom_ms, "ms_isolated": iso_ms,
+                # the persistent products leave some SMs to the levels >= 2
+                # chain: the fraction of the peak of the SMs they run on
+                "sms": int(st.get("persistent_ctas") or N_SM),
+                "frac_of_its_sms": ach / (peak_tf * (st.get("persistent_ctas") or N_SM) / N_SM),
                 "frac_isolated": flops / (iso_ms * 1e-3) / 1e12 / peak_tf,
                 # the streaming model (every complex MAC reads a source and a
                 # kernel value, 16 B in FP32): what HBM would have to deliver

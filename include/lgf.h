@@ -188,6 +188,8 @@ lgf_status lgf_plan_create_multi(const int32_t *block_ijk, const int64_t *block_
  *   merged_level01     1 if levels 0 and 1 share one product pass (nw[1] is
  *                      then the level-0 spectrum size)
  *   n_problems         independent problems in the plan (lgf_plan_create_multi)
+ *   persistent_ctas    CTAs (one per SM) of the persistent level-0 products, 0 if
+ *                      that level uses another form
  *   n_levels           the largest level count of its problems
  */
 #define LGF_MAX_LEVELS 24
@@ -201,6 +203,7 @@ typedef struct {
     int64_t workspace_bytes;
     int32_t merged_level01;
     int32_t n_problems;
+    int32_t persistent_ctas;
 } lgf_plan_stats;
 
 lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);

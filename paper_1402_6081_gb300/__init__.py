@@ -131,7 +131,7 @@ class lgf_plan_stats(ctypes.Structure):
                 ("groups", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32),
-                ("n_problems", ctypes.c_int32)]
+                ("n_problems", ctypes.c_int32), ("persistent_ctas", ctypes.c_int32)]
 
 
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
@@ -204,7 +204,8 @@ def lgf_plan_get_stats(plan: int) -> dict:
             "fft_size_interval": st.fft_size_interval, "pairs": list(st.pairs[: L + 1]),
             "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
             "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes,
-            "merged_level01": st.merged_level01, "n_problems": st.n_problems}
+            "merged_level01": st.merged_level01, "n_problems": st.n_problems,
+            "persistent_ctas": st.persistent_ctas}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:

@@ -1205,6 +1205,7 @@ lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
     }
     st->merged_level01 = plan->merged ? 1 : 0;
     st->n_problems = plan->n_problems;
+    st->persistent_ctas = uses_persist(plan, 0) ? plan->lev[0].pp.n_cta : 0;
     if (plan->merged && plan->Lmac >= 1) st->nw[1] = nw_of(plan->S0);
     size_t b = 0;
     lgf_plan_workspace_bytes(plan, &b);
