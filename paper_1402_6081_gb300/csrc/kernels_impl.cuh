@@ -339,9 +339,30 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x,
         : "memory");
 }
 
-// A chunk of 343 coefficient rows arrives as two boxes of kTmaRows rows
-// (the second box's last row lies past the table and is zero-filled).
-constexpr int kTmaRows = 172;
+// The 343-offset kernel tables store rows 171..342 only (kSymRows rows);
+// row d < 171 is the complex conjugate of row 342 - d (offset -d).  A chunk's
+// stored rows arrive as one tensor box into rows 171..342 of the chunk's
+// shared-memory table, and the first 171 rows are filled by conjugation.
+constexpr int kSymRows = 172, kSymFirst = 171;
+
+template <typename T>
+__device__ __forceinline__ cx<T> conjx(cx<T> v) { return {v.x, -v.y}; }
+
+// coefficient of 7^3-table row d at frequency w, from the stored half table
+template <typename T, int64_t NWS>
+__device__ __forceinline__ cx<T> coef_sym(const cx<T>* __restrict__ kh, int d, int64_t w) {
+    return d >= kSymFirst ? ldg_cx(kh + int64_t(d - kSymFirst) * NWS + w)
+                          : conjx(ldg_cx(kh + int64_t(kSymFirst - d) * NWS + w));
+}
+
+// rows 0..170 of a [343][32] shared table from its rows 171..342
+template <typename T>
+__device__ __forceinline__ void mirror_rows(cx<T>* sk, int tid, int nthreads) {
+    for (int i = tid; i < kSymFirst * 32; i += nthreads) {
+        const int r = i >> 5, l = i & 31;
+        sk[i] = conjx(sk[(2 * kSymFirst - r) * 32 + l]);
+    }
+}
 
 constexpr int kMacWarps = 12;
 
@@ -420,8 +441,9 @@ __device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], 
 }
 
 // The 343 coefficient rows of the frequencies w0 .. w0+31 into shared memory
-// ([343][32], zero past NW): eight independent loads per thread in flight
-// before their stores, so a CTA keeps enough requests outstanding to stream.
+// ([343][32], zero past NW) from the stored half table: eight independent
+// loads per thread in flight before their stores, so a CTA keeps enough
+// requests outstanding to stream.
 template <typename T, int64_t NW, int64_t NWS, int NT>
 __device__ __forceinline__ void stage_coefficients(cx<T>* __restrict__ sk, const cx<T>* __restrict__ kh, int64_t w0,
                                                    int tid) {
@@ -432,7 +454,7 @@ __device__ __forceinline__ void stage_coefficients(cx<T>* __restrict__ sk, const
         for (int j = 0; j < kBatch; ++j) {
             const int i = base + j * NT + tid;
             const int64_t w = w0 + (i & 31);
-            v[j] = (i < kTotal && w < NW) ? ldg_cx(kh + int64_t(i >> 5) * NWS + w) : czero<T>();
+            v[j] = (i < kTotal && w < NW) ? coef_sym<T, NWS>(kh, i >> 5, w) : czero<T>();
         }
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) {
@@ -458,24 +480,25 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [2 kTmaRows][32]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(cx<T>) * 2 * kTmaRows * 32);
+    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(cx<T>) * 343 * 32);
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     if (use_tma) {
-        // the chunk's rows as two tensor boxes (x in reals: 2 per complex)
+        // the chunk's stored rows as one tensor box (x in reals: 2 per complex)
         if (tid == 0) {
             mbar_init(bar, 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            mbar_expect_tx(bar, unsigned(sizeof(cx<T>) * 2 * kTmaRows * 32));
-            tma_2d(sk, &tmap, int(2 * w0), 0, bar);
-            tma_2d(sk + kTmaRows * 32, &tmap, int(2 * w0), kTmaRows, bar);
+            mbar_expect_tx(bar, unsigned(sizeof(cx<T>) * kSymRows * 32));
+            tma_2d(sk + kSymFirst * 32, &tmap, int(2 * w0), 0, bar);
         }
         __syncthreads();
         if (!mbar_wait(bar, 0)) {
             if (tid == 0) atomicExch(err, 1);
             return;
         }
+        mirror_rows(sk, tid, 32 * kMacWarps);
+        __syncthreads();
     } else {
         stage_coefficients<T, NW, NWS, 32 * kMacWarps>(sk, kh, w0, tid);
         __syncthreads();
@@ -717,7 +740,7 @@ __global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T
     for (int i = tid; i < 343 * 64; i += 32 * kMac2Warps) {
         const int d = i >> 6, lane = i & 63;
         const int64_t w = w0 + lane;
-        sk[i] = w < NW ? ldg_cx(kh + int64_t(d) * NWS + w) : czero<T>();
+        sk[i] = w < NW ? coef_sym<T, NWS>(kh, d, w) : czero<T>();
     }
     __syncthreads();
     const int g0 = blockIdx.x * groups_per_cta;
@@ -910,7 +933,8 @@ __device__ __forceinline__ void persist_block(cx<float> (&acc)[8], const cx<floa
         }
 }
 
-constexpr unsigned kPersistBuf = 2u * kTmaRows * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
+constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
+constexpr unsigned kPersistFill = unsigned(kSymRows) * 32u * sizeof(cx<float>);   // bytes copied per chunk
 constexpr size_t kPersistSmem = 2 * size_t(kPersistBuf) + 64;
 
 template <int S>
@@ -922,9 +946,10 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][2 kTmaRows][32]
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * kPersistBuf);   // [2]
-    int* ctr = reinterpret_cast<int*>(full + 2);                             // [2] next position
+    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][343][32]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * kPersistBuf);   // [2] copy landed
+    uint64_t* ready = full + 2;                                                // [2] rows mirrored
+    int* ctr = reinterpret_cast<int*>(ready + 2);                            // [2] next position
     int* done = ctr + 2;                                                     // [2] warps finished
     const long long u0 = cta_units[blockIdx.x], u1 = cta_units[blockIdx.x + 1];
     if (u0 >= u1) return;
@@ -933,40 +958,55 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
+        mbar_init(&ready[0], 1);
+        mbar_init(&ready[1], 1);
         ctr[0] = ctr[1] = 0;
         done[0] = done[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // one warp issues the 343 row copies of chunk c (256 bytes each)
-    auto fill = [&](long long c) {
+    // one warp loads chunk c: the stored rows by one tensor box (or 172 row
+    // copies), then, once they landed, the mirrored rows by conjugation;
+    // ready[b] releases the chunk to every warp
+    auto issue = [&](long long c) {
         const int b = int((c - c0) & 1);
-        cx<float>* dst = buf + b * (2 * kTmaRows * 32);
+        cx<float>* dst = buf + b * (343 * 32) + kSymFirst * 32;
         if (use_tma) {
-            // two tensor boxes (x in reals: 2 per complex)
             if (lane == 0) {
-                mbar_expect_tx(&full[b], kPersistBuf);
+                mbar_expect_tx(&full[b], kPersistFill);
                 tma_2d(dst, &tmap, int(c * 64), 0, &full[b]);
-                tma_2d(dst + kTmaRows * 32, &tmap, int(c * 64), kTmaRows, &full[b]);
             }
             return;
         }
-        if (lane == 0) mbar_expect_tx(&full[b], 343u * 256u);
+        if (lane == 0) mbar_expect_tx(&full[b], kPersistFill);
         __syncwarp();
         const cx<float>* src = kh + c * 32;
-        for (int d = lane; d < 343; d += 32) bulk_g2s(dst + d * 32, src + int64_t(d) * NWS, 256u, &full[b]);
+        for (int r = lane; r < kSymRows; r += 32) bulk_g2s(dst + r * 32, src + int64_t(r) * NWS, 256u, &full[b]);
+    };
+    auto finish = [&](long long c) {
+        const int b = int((c - c0) & 1);
+        if (mbar_wait(&full[b], unsigned(((c - c0) >> 1) & 1))) {
+            cx<float>* t = buf + b * (343 * 32);
+            for (int r = 0; r < kSymFirst; ++r) t[r * 32 + lane] = conjx(t[(2 * kSymFirst - r) * 32 + lane]);
+        } else if (lane == 0) {
+            atomicExch(err, 1);
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[b])) : "memory");
     };
     if (warp == 0) {
-        fill(c0);
-        if (c1 > c0) fill(c0 + 1);
+        issue(c0);
+        if (c1 > c0) issue(c0 + 1);
+        finish(c0);
+        if (c1 > c0) finish(c0 + 1);
     }
     for (long long c = c0; c <= c1; ++c) {
         const int b = int((c - c0) & 1);
-        if (!mbar_wait(&full[b], unsigned(((c - c0) >> 1) & 1))) {
+        if (!mbar_wait(&ready[b], unsigned(((c - c0) >> 1) & 1))) {
             if (lane == 0) atomicExch(err, 1);
             return;
         }
-        const cx<float>* sk = buf + b * (2 * kTmaRows * 32) + lane;
+        const cx<float>* sk = buf + b * (343 * 32) + lane;
         const int pb = c == c0 ? int(u0 % n_groups) : 0;
         const int pe = c == c1 ? int((u1 - 1) % n_groups) + 1 : n_groups;
         const int64_t w = c * 32 + lane;
@@ -1022,7 +1062,8 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
             }
             if (c + 2 <= c1) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fill(c + 2);
+                issue(c + 2);
+                finish(c + 2);
             }
         }
     }
@@ -1446,7 +1487,7 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
         kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
         return cudaGetLastError();
     }
-    const size_t smem = sizeof(dev::cx<T>) * 2 * dev::kTmaRows * 32 + 16;
+    const size_t smem = sizeof(dev::cx<T>) * 343 * 32 + 16;
     auto kern = dev::k_mac_interval<T, S>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;

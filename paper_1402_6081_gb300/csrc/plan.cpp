@@ -168,7 +168,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // rows x NWS complex values viewed as rows x 2 NWS reals; boxes of 32
-// complex values (64 reals) by 172 rows
+// complex values (64 reals) by 172 rows (a whole stored half-table chunk)
 static bool encode_table_map(SpecEntry& e, int rows, int64_t nws, int prec) {
     auto enc = tensor_map_encoder();
     if (!enc || rows < 172) return false;
@@ -206,25 +206,31 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
     const int n = kind == kInterval ? n_b + 1 : n_b;
     const int V = near ? 2 * n_b - 1 : kind == kBlock ? 4 * n_b - 1 : 4 * n_b;
     auto tab = green_abs_table(h, V);
-    const int nd = near ? 27 : 343;
+    // The kernel vector of -d is that of d reflected (G is even and the
+    // window |m_a| <= n - 1 symmetric), so its spectrum is the complex
+    // conjugate: the 343-offset tables keep only the rows id >= 171 (d = 0 and
+    // the offsets after it in x-fastest order); row id < 171 is the conjugate
+    // of row 342 - id.  The 27-offset table is kept whole.
+    const int nd = near ? 27 : 172;
+    const int first = near ? 0 : 171;
     const int64_t NW = nw_of(S), NWS = nws_of(S);
     std::vector<std::complex<double>> all(size_t(nd) * NWS, 0.0);
     std::vector<int> todo;
-    for (int id = 0; id < nd; ++id) {
-        const int r = near ? 3 : 7, o = near ? 1 : 3;
+    for (int row = 0; row < nd; ++row) {
+        const int id = first + row, r = near ? 3 : 7, o = near ? 1 : 3;
         const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
         const bool is_near = std::abs(d[0]) <= 1 && std::abs(d[1]) <= 1 && std::abs(d[2]) <= 1;
-        if (kind != kInterval || !is_near) todo.push_back(id);
+        if (kind != kInterval || !is_near) todo.push_back(row);
     }
     unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
     for (unsigned w = 0; w < nthr; ++w)
         th.emplace_back([&, w] {
             for (size_t t = w; t < todo.size(); t += nthr) {
-                const int id = todo[t];
+                const int row = todo[t], id = first + row;
                 const int r = near ? 3 : 7, o = near ? 1 : 3;
                 const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
-                kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(id) * NWS]);
+                kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(row) * NWS]);
             }
         });
     for (auto& t : th) t.join();
@@ -249,7 +255,7 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
         ce = cudaMemcpy(e->ptr, f.data(), e->bytes, cudaMemcpyHostToDevice);
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "spectra upload");
-    e->has_tmap = nd == 343 && encode_table_map(*e, nd, NWS, prec);
+    e->has_tmap = !near && encode_table_map(*e, nd, NWS, prec);
     g_spec_cache[key] = e;
     out = e;
     return ok();
