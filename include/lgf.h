@@ -253,6 +253,20 @@ lgf_status lgf_batch_launch(lgf_batch batch, void *stream);
 lgf_status lgf_batch_destroy(lgf_batch batch);
 
 /*
+ * lgf_selftest_bounded_wait - diagnostic of the bounded device waits (no
+ * counterpart in the paper).  The library's kernels never spin without a
+ * limit: a wait that runs out sets a status word and the kernel returns, so
+ * a stalled producer turns into an error code instead of a hang.  This call
+ * runs one such wait on an mbarrier phase: complete != 0 completes the phase
+ * (returns LGF_OK); complete == 0 leaves it pending, so the wait gives up
+ * after limit_us microseconds of the GPU's global timer and the call returns
+ * LGF_ERR_TIMEOUT with the context still usable.
+ *   limit_us   1 .. 2000000
+ * Synchronous (device-wide synchronize).
+ */
+lgf_status lgf_selftest_bounded_wait(int32_t complete, int32_t limit_us);
+
+/*
  * lgf_solve_host - lgf_solve with host buffers: copies f to the plan's device
  * staging buffer, solves, copies u back, and waits for the stream.
  *   f_host, u_host  host pointers of n_points values (pinned memory is faster)

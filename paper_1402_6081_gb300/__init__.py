@@ -50,6 +50,7 @@ _SIGS = {
     "lgf_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lgf_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "lgf_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "lgf_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -258,6 +259,12 @@ def lgf_solve_host(plan: int, f_host, u_host, stream=None) -> None:
     fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data
     up = u_host.data_ptr() if hasattr(u_host, "data_ptr") else u_host.ctypes.data
     _check(library().lgf_solve_host(plan, fp, up, _stream_ptr(stream)), "lgf_solve_host")
+
+
+def lgf_selftest_bounded_wait(complete: int, limit_us: int) -> None:
+    """Run one bounded device wait (see include/lgf.h); raises LgfError with
+    LGF_ERR_TIMEOUT when it runs out."""
+    _check(library().lgf_selftest_bounded_wait(complete, limit_us), "lgf_selftest_bounded_wait")
 
 
 def lgf_plan_sync(plan: int) -> None:

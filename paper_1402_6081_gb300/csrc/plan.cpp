@@ -3,9 +3,12 @@
 // precomp), device workspace, and the launch sequence of Steps 1-3.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -385,9 +388,31 @@ struct lgf_plan_s {
 
 namespace lgf {
 
+// Fault injection for tests: with LGF_FAULT_ALLOC_AT=k in the environment the
+// k-th workspace allocation after the variable took that value (counting
+// from 1) fails as if the device were out of memory.
+static bool injected_alloc_failure() {
+    static std::mutex mu;
+    static std::string seen;
+    static long long count = 0;
+    const char* v = std::getenv("LGF_FAULT_ALLOC_AT");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!v || !*v) {
+        seen.clear();
+        return false;
+    }
+    if (seen != v) {
+        seen = v;
+        count = 0;
+    }
+    return ++count == std::atoll(v);
+}
+
 static lgf_status dalloc(lgf_plan_s* P, size_t bytes, void** out, bool zero) {
     *out = nullptr;
     if (bytes == 0) return ok();
+    if (injected_alloc_failure())
+        return fail(LGF_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes: injected failure");
     cudaError_t e = cudaMalloc(out, bytes);
     if (e != cudaSuccess) {
         *out = nullptr;
@@ -445,6 +470,18 @@ struct HostPlan {
     std::vector<int64_t> pairs, intervals, groups;   // levels 0..L
 };
 
+// Bounds checks of the tables a plan hands to its kernels, on the host before
+// upload: every index a kernel dereferences lies inside the buffer it
+// addresses.  A violation is an internal error and fails the plan.
+static lgf_status check_range(const char* what, const std::vector<int>& v, long long lo, long long hi) {
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i] < lo || v[i] >= hi)
+            return fail(LGF_ERR_INVALID_ARG, std::string("plan table check failed: ") + what + "[" + std::to_string(i) +
+                                                 "] = " + std::to_string(v[i]) + " outside [" + std::to_string(lo) +
+                                                 ", " + std::to_string(hi) + ")");
+    return ok();
+}
+
 // Whether level l's products run in the persistent kernel: FP32 plans with
 // interval_kernel 4 (or the default 0), at the interval levels and at level 0
 // when it carries the merged level-0/level-1 products.  Its 24 warps share the
@@ -484,6 +521,19 @@ static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<in
             pairs.push_back({q, (2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)});
         }
         start[size_t(pos) + 1] = int(pairs.size());
+    }
+    {
+        std::vector<int> src, centre;
+        for (const PairSrc& q : pairs) {
+            src.push_back(q.src);
+            centre.push_back(q.centre);
+        }
+        lgf_status s;
+        if ((s = check_range("pair source group", src, 0, G)) != LGF_OK) return s;
+        // the 27 rows read around a centre stay inside the 343-row table
+        if ((s = check_range("pair centre row", centre, 57, 343 - 57)) != LGF_OK) return s;
+        for (int pos = 0; pos < G; ++pos)
+            if (start[size_t(pos)] > start[size_t(pos) + 1]) return fail(LGF_ERR_INVALID_ARG, "plan table check failed: pair starts");
     }
     int n_sm = 0;
     LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
@@ -739,6 +789,17 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                 for (const R2CItem& it : T.r2c)
                     items.push_back({l <= 1 ? it.src + boff[p] : it.src + 8 * go[p], it.dst + 8 * go[p]});
             }
+            if ((s = check_range("neighbour group", gn, -1, D.n_groups)) != LGF_OK) return s;
+            {
+                std::vector<int> src, dst;
+                for (const R2CItem& it : items) {
+                    src.push_back(it.src);
+                    dst.push_back(it.dst);
+                }
+                if ((s = check_range("forward FFT source", src, 0, l <= 1 ? P->n_blocks : static_cast<long long>(slots))) != LGF_OK)
+                    return s;
+                if ((s = check_range("forward FFT slot", dst, 0, static_cast<long long>(slots))) != LGF_OK) return s;
+            }
             if ((s = upload(P, gn, &D.gnbr)) != LGF_OK) return s;
             {
                 std::vector<int> cnt(size_t(D.n_groups), 0), ord(size_t(D.n_groups));
@@ -770,6 +831,9 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                     for (int slot : hp[p].lev[size_t(l)].iv_slot) items.push_back({slot + 8 * go[p], slot + 8 * go[p], -1});
                 }
                 D.n_c2r = int(items.size());
+                for (const C2RItem& it : items)
+                    if (it.src < 0 || it.src >= static_cast<long long>(slots) || it.dst < 0 || it.dst >= static_cast<long long>(slots))
+                        return fail(LGF_ERR_INVALID_ARG, "plan table check failed: inverse FFT slot");
                 if ((s = upload(P, items, &D.c2r)) != LGF_OK) return s;
             }
         }
@@ -784,6 +848,9 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                     child.push_back(c < 0 ? -1 : l == 2 ? c + boff[p] : c + 8 * goff[size_t(l) - 1][p]);
             }
             D.n_reg = int(par.size());
+            if ((s = check_range("Reg child", child, -1, l == 2 ? P->n_blocks : 8LL * ngroups[size_t(l) - 1])) != LGF_OK)
+                return s;
+            if ((s = check_range("Reg parent slot", par, 0, static_cast<long long>(slots))) != LGF_OK) return s;
             if ((s = upload(P, child, &D.reg_child)) != LGF_OK) return s;
             if ((s = upload(P, par, &D.reg_parent)) != LGF_OK) return s;
         }
@@ -799,6 +866,9 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                     for (size_t i = 0; i < T.int_slot.size(); ++i) bl.push_back(boff[p] + int(i));
             }
             D.n_int = int(sl.size());
+            if ((s = check_range("Interp slot", sl, 0, static_cast<long long>(slots))) != LGF_OK) return s;
+            if ((s = check_range("Interp parent slot", pa, 0, 8LL * ngroups[size_t(l) + 1])) != LGF_OK) return s;
+            if ((s = check_range("Interp block", bl, 0, P->n_blocks)) != LGF_OK) return s;
             if ((s = upload(P, sl, &D.int_slot)) != LGF_OK) return s;
             if ((s = upload(P, pa, &D.int_parent)) != LGF_OK) return s;
             if (l == 1 && (s = upload(P, bl, &D.int_block)) != LGF_OK) return s;
@@ -817,6 +887,10 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                                  has_ut1 ? s0[size_t(b)] + 8 * goff[1][p] : -1});
         }
         P->n_out = int(items.size());
+        const long long s0 = 8LL * ngroups[0], s1 = Lmac >= 1 ? 8LL * ngroups[1] : 0;
+        for (const C2RItem& it : items)
+            if (it.src < 0 || it.src >= s0 || it.dst < 0 || it.dst >= P->n_blocks || it.aux >= s1 || it.aux < -1)
+                return fail(LGF_ERR_INVALID_ARG, "plan table check failed: output item");
         lgf_status s = upload(P, items, &P->out_items);
         if (s != LGF_OK) return s;
     }
@@ -850,7 +924,9 @@ static cudaError_t timed(lgf_plan_s* P, const char* name, cudaStream_t st, F&& l
     const int k = P->ev_used;
     const bool rec = 2 * (k + 1) <= int(P->ev.size());
     if (rec) cudaEventRecord(P->ev[size_t(2 * k)], st);
+    nvtxRangePushA(name);   // host-side range per launch, seen by profilers
     cudaError_t e = launch();
+    nvtxRangePop();
     if (rec) {
         cudaEventRecord(P->ev[size_t(2 * k + 1)], st);
         P->ev_name[size_t(k)] = name;
@@ -1231,9 +1307,13 @@ lgf_status lgf_solve(lgf_plan plan, const void* f_dev, void* u_dev, void* stream
     lgf_status s = check_device(plan);
     if (s != LGF_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (plan->prec == LGF_FP64)
-        return solve_impl<double>(plan, static_cast<const double*>(f_dev), static_cast<double*>(u_dev), st);
-    return solve_impl<float>(plan, static_cast<const float*>(f_dev), static_cast<float*>(u_dev), st);
+    nvtxRangePushA("lgf_solve");
+    const lgf_status r =
+        plan->prec == LGF_FP64
+            ? solve_impl<double>(plan, static_cast<const double*>(f_dev), static_cast<double*>(u_dev), st)
+            : solve_impl<float>(plan, static_cast<const float*>(f_dev), static_cast<float*>(u_dev), st);
+    nvtxRangePop();
+    return r;
 }
 
 lgf_status lgf_solve_batch(const lgf_plan* plans, const void* const* f_dev, void* const* u_dev, int32_t n,
