@@ -322,6 +322,55 @@ def irregular_run(torch, lgfm, steps: int, flush):
     return out
 
 
+def fft_conv_run(torch, lgfm, steps: int, flush):
+    """The FFT-convolution special case (Sec. 4, "FFT Conv."): every 16^3 block
+    an isolated one-block domain, u_b = G * f_b by one padded 32^3 R2C, one
+    spectral product and one truncated C2R (lgf_solve_blocks_noalloc, 232
+    blocks per call), the 512 blocks of the 128^3 torus per step, FP32.  Work is
+    counted as 5 N log2 N flop per real 32^3 transform (both directions) plus
+    the product; the fraction is of the FP32 FMA peak."""
+    p = W.config(1)
+    n_b = p.n_b
+    per_call = lgfm.lgf_noalloc_max_blocks(n_b, lgfm.LGF_FP32)
+    f = torch.from_numpy(p.f).float().cuda()
+    u = torch.empty_like(f)
+    nblk = len(p.blocks)
+    stream = torch.cuda.Stream()
+
+    def one_pass():
+        for b0 in range(0, nblk, per_call):
+            nb = min(per_call, nblk - b0)
+            lgfm.lgf_solve_blocks_noalloc(f[b0:b0 + nb], u[b0:b0 + nb], nb, n_b, lgfm.LGF_FP32, stream)
+
+    with torch.cuda.stream(stream):
+        one_pass()
+        for _ in range(3):
+            one_pass()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            one_pass()
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    S = 2 * n_b
+    n3 = S ** 3
+    flops_block = 2 * 5.0 * n3 * np.log2(n3) / 2 + 8.0 * (S // 2 + 1) * S * S
+    tf = nblk * flops_block / (ms * 1e-3) / 1e12
+    peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"value": p.n_points / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms, "steps": steps,
+            "launch_calls_per_step": -(-nblk // per_call),
+            "roofline": {"bound": "alu", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
+                         "algorithmic": "per block: 5 N log2 N / 2 per real 32^3 transform x 2 + 8 flop per "
+                                        "complex product",
+                         "hbm_gbs_f_and_u": 8.0 * p.n_points / (ms * 1e-3) / 1e9},
+            "config": {"workload": "fft_conv_16cubed_blocks", "blocks": nblk, "points": p.n_points,
+                       "l2": "flushed: 256 MiB write before every timed step"}}
+
+
 def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
     """Poisson arrivals (200/s, seed 1) of torus solves with point counts
     log-uniform in 2^12..2^24, admitted under a 120 GB HBM budget, FP32 form
@@ -384,6 +433,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-solve batched workload")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson-arrival serving workload")
     ap.add_argument("--no-irregular", action="store_true", help="skip the 512^3 irregular-domain workload")
+    ap.add_argument("--no-fft-conv", action="store_true", help="skip the single-block FFT-convolution workload")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -583,6 +633,11 @@ def main():
             out["batch"] = batch_run(torch, lgfm, max(3, min(200, args.steps // 10)), 3, flush)
         except Exception as exc:       # reported in the line, the headline stands
             out["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if world == 1 and not args.no_fft_conv:
+        try:
+            out["fft_conv"] = fft_conv_run(torch, lgfm, max(3, min(100, args.steps // 20)), flush)
+        except Exception as exc:
+            out["fft_conv"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and not args.no_irregular:
         try:
             out["irregular"] = irregular_run(torch, lgfm, max(3, min(50, args.steps // 40)), flush)
