@@ -201,6 +201,18 @@ def run_reference(args):
     }))
 
 
+def replica_rate(total_ms: float, points: int, steps: int, world: int, dist=None, device: str = "cpu"):
+    """Weak scaling over replicas: every rank solves its own copy of the
+    workload; the job's time is the slowest rank's (max over ranks), and the
+    job's rate counts the points of all ranks.  Returns (max ms, points/s)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * points * steps / (total_ms * 1e-3)
+
+
 def batch_run(torch, lgfm, steps: int, warmup: int, flush):
     """64 independent uneven solves (log-uniform 32^3..192^3 boxes, 8^3 or 16^3
     blocks, Gaussian-blob sources) as one CUDA-graph batch: one multi-problem
@@ -520,12 +532,7 @@ def main():
     clk = clocks.stop()
     ktimes, per_solve_launches = lgfm.lgf_plan_timings(s32.plan)
     lgfm.lgf_plan_set_timing(s32.plan, 0)
-    total_ms = float(sum(ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * npts * args.steps / (total_ms * 1e-3)
+    total_ms, value = replica_rate(float(sum(ms)), npts, args.steps, world, dist, "cuda")
 
     # the same kernels once more with every launch on one stream, so the
     # dominant kernel is also timed without other chains sharing the SMs
