@@ -111,16 +111,19 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *   near_kernel        product kernel of level 0: 0 = default, 1 = fully
  *                      unrolled 4^3-source form, 2 = half-plane pipelined form
  *   interval_kernel    product kernel of levels >= 1 (and of the merged
- *                      level-0/1 pass): 0 = default (4 for FP32 plans, 1 for
- *                      FP64), 1 = one frequency per thread, one CTA per
+ *                      level-0/1 pass): 0 = default (5 for FP32 plans where a
+ *                      level has >= 48 sibling groups, else 1), 1 = one
+ *                      frequency per thread, one CTA per
  *                      (frequency chunk, group range), 2 = two frequencies per
  *                      thread, 3 = two sibling groups per warp sharing
  *                      coefficient loads, 4 = persistent: one CTA per SM over
  *                      a plan-time range of equal work, coefficient chunks
  *                      staged by bulk copies into two shared-memory buffers
- *                      (2, 3 and 4: FP32 only; FP64 plans use 1).  A wait in
- *                      form 4 that runs out (about 2 s) sets a flag that
- *                      lgf_plan_sync reports as LGF_ERR_CUDA.
+ *                      5 = form 4 with the products as packed two-wide FP32
+ *                      FMAs (fma.rn.f32x2), 16 warps per CTA
+ *                      (2, 3, 4 and 5: FP32 only; FP64 plans use 1).  A wait
+ *                      in forms 4 and 5 that runs out (about 2 s) sets a flag
+ *                      that lgf_plan_sync reports as LGF_ERR_CUDA.
  *   single_stream      1 = run every kernel of a solve on the caller's stream;
  *                      0 (default) = the level-1 chain and the levels >= 2
  *                      chain run on two plan-owned streams forked from and

@@ -898,6 +898,7 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
 // chunk after next.  Each group's sources come from a flat list (source group,
 // centre coefficient row), so the inner loop has no neighbour-mask logic.
 constexpr int kPersistWarps = 24;
+constexpr int kPersistWarpsPacked = 16;   // the packed form holds more registers
 
 __device__ __forceinline__ PairSrc ldg_pair(const PairSrc* p) {
     const int2 v = __ldg(reinterpret_cast<const int2*>(p));
@@ -933,12 +934,55 @@ __device__ __forceinline__ void persist_block(cx<float> (&acc)[8], const cx<floa
         }
 }
 
+// Packed form of the 8 x 8 sibling products (fma.rn.f32x2: two FP32 FMAs per
+// instruction).  With F = Fx + i Fy and K = Kx + i Ky, A accumulates
+// (Fx Kx, Fx Ky) and B accumulates (Fy Kx, Fy Ky), both against K as stored;
+// the complex sum is (A.x - B.y) + i (A.y + B.x).  Half the FMA instructions
+// of persist_block for the same coefficient loads.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void ffma2(uint64_t& d, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ cx<float> unpack_sum(uint64_t A, uint64_t B) {
+    float ax, ay, bx, by;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(ax), "=f"(ay) : "l"(A));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(bx), "=f"(by) : "l"(B));
+    return {ax - by, ay + bx};
+}
+__device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
+                                                     const cx<float>* kb) {
+    uint64_t kk[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] =
+                    *reinterpret_cast<const uint64_t*>(kb + (dx + 7 * dy + 49 * dz) * 32);
+#pragma unroll
+    for (int cs = 0; cs < 8; ++cs) {
+        const uint64_t fx = pk2(F[cs].x, F[cs].x), fy = pk2(F[cs].y, F[cs].y);
+#pragma unroll
+        for (int ct = 0; ct < 8; ++ct) {
+            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
+            const uint64_t k = kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+            ffma2(A[ct], fx, k);
+            ffma2(B[ct], fy, k);
+        }
+    }
+}
+
 constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
 constexpr unsigned kPersistFill = unsigned(kSymRows) * 32u * sizeof(cx<float>);   // bytes copied per chunk
 constexpr size_t kPersistSmem = 2 * size_t(kPersistBuf) + 64;
 
-template <int S>
-__global__ void __launch_bounds__(32 * kPersistWarps, 1)
+template <int S, int WARPS, bool PACKED>
+__global__ void __launch_bounds__(32 * WARPS, 1)
     k_mac_persist(const cx<float>* __restrict__ fh, const cx<float>* __restrict__ kh, cx<float>* __restrict__ uh,
                   const PairSrc* __restrict__ pairs, const int* __restrict__ start, const int* __restrict__ order,
                   const long long* __restrict__ cta_units, int n_groups, int* __restrict__ err,
@@ -1018,8 +1062,16 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
             if (pos >= pe) break;
             const int p0 = __ldg(start + pos), p1 = __ldg(start + pos + 1);
             cx<float> acc[8];
+            [[maybe_unused]] uint64_t A[8], B[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[i] = czero<float>();
+            for (int i = 0; i < 8; ++i) {
+                acc[i] = czero<float>();
+                if constexpr (PACKED) A[i] = B[i] = 0ull;
+            }
+            auto block = [&](const cx<float> (&F)[8], int centre) {
+                if constexpr (PACKED) persist_block_packed(A, B, F, sk + centre * 32);
+                else persist_block(acc, F, sk + centre * 32);
+            };
             if (p1 > p0) {
                 cx<float> Fa[8], Fb[8];
                 PairSrc pa = ldg_pair(pairs + p0), pq{0, 0};
@@ -1030,16 +1082,20 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
                         pq = ldg_pair(pairs + p + 1);
                         persist_load<S>(Fb, fh, pq.src, wc);
                     }
-                    persist_block(acc, Fa, sk + pa.centre * 32);
+                    block(Fa, pa.centre);
                     if (!hb) break;
                     const bool ha = p + 2 < p1;
                     if (ha) {
                         pa = ldg_pair(pairs + p + 2);
                         persist_load<S>(Fa, fh, pa.src, wc);
                     }
-                    persist_block(acc, Fb, sk + pq.centre * 32);
+                    block(Fb, pq.centre);
                     if (!ha) break;
                 }
+            }
+            if constexpr (PACKED) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = unpack_sum(A[i], B[i]);
             }
             if (w < NW) {
                 cx<float>* out = uh + int64_t(__ldg(order + pos)) * (8 * NWS) + w;
@@ -1053,7 +1109,7 @@ __global__ void __launch_bounds__(32 * kPersistWarps, 1)
         int last = 0;
         if (lane == 0) {
             __threadfence_block();
-            last = atomicAdd(&done[b], 1) == kPersistWarps - 1;
+            last = atomicAdd(&done[b], 1) == WARPS - 1;
         }
         if (__shfl_sync(0xffffffffu, last, 0)) {
             if (lane == 0) {
@@ -1517,21 +1573,28 @@ cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, co
 #undef LGF_MACI
 }
 
-template <int S>
+template <int S, int WARPS, bool PACKED>
 static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp,
                                       cudaStream_t st) {
-    auto kern = dev::k_mac_persist<S>;
+    auto kern = dev::k_mac_persist<S, WARPS, PACKED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::kPersistSmem));
     if (e != cudaSuccess) return e;
     if (pp.n_groups == 0 || pp.n_cta == 0) return cudaSuccess;
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (pp.tmap) map = *pp.tmap;
-    kern<<<pp.n_cta, 32 * dev::kPersistWarps, dev::kPersistSmem, st>>>(
+    kern<<<pp.n_cta, 32 * WARPS, dev::kPersistSmem, st>>>(
         static_cast<const dev::cx<float>*>(fh), static_cast<const dev::cx<float>*>(kh),
         static_cast<dev::cx<float>*>(uh), pp.pairs, pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err, map,
         pp.tmap ? 1 : 0);
     return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t launch_mac_persist_form(const void* fh, const void* kh, void* uh, const PersistPlan& pp,
+                                           cudaStream_t st) {
+    if (pp.packed) return launch_mac_persist<S, dev::kPersistWarpsPacked, true>(fh, kh, uh, pp, st);
+    return launch_mac_persist<S, dev::kPersistWarps, false>(fh, kh, uh, pp, st);
 }
 
 template <typename T>
@@ -1541,7 +1604,7 @@ cudaError_t Launch<T>::mac_persist(const void* fh, const void* kh, void* uh, con
         return cudaErrorInvalidValue;
     } else {
 #define LGF_MACP(SS) \
-    case SS: return launch_mac_persist<SS>(fh, kh, uh, pp, st);
+    case SS: return launch_mac_persist_form<SS>(fh, kh, uh, pp, st);
         switch (S) {
             LGF_MACP(8) LGF_MACP(10) LGF_MACP(16) LGF_MACP(17) LGF_MACP(18) LGF_MACP(32) LGF_MACP(33) LGF_MACP(34)
             LGF_MACP(36)

@@ -77,6 +77,7 @@ struct PersistPlan {
     const long long* cta_units = nullptr;    // n_cta + 1
     int n_groups = 0, n_cta = 0;
     int* err = nullptr;
+    bool packed = false;                 // fma.rn.f32x2 form of the products
 };
 
 // Launchers (kernels.cu); T = float or double.  All asynchronous on `stream`.

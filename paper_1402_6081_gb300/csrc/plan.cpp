@@ -494,12 +494,12 @@ static bool shares_sms(const lgf_plan_s* P) {
 }
 static bool uses_persist(const lgf_plan_s* P, int l) {
     if (P->prec != LGF_FP32) return false;
-    if (P->interval_kernel != 0 && P->interval_kernel != 4) return false;
+    if (P->interval_kernel != 0 && P->interval_kernel != 4 && P->interval_kernel != 5) return false;
     if (l == 0 && !P->merged) return false;
     // beside shared-SM level-0 products, levels >= 2 keep the
     // one-CTA-per-chunk form, which fits on the SMs left to them
     if (l >= 2 && shares_sms(P)) return false;
-    return P->interval_kernel == 4 || P->lev[size_t(l)].n_groups >= 48;
+    return P->interval_kernel >= 4 || P->lev[size_t(l)].n_groups >= 48;
 }
 
 // Work lists of the persistent kernel for one level (see PersistPlan); the
@@ -566,6 +566,7 @@ static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<in
     D.pp.n_groups = G;
     D.pp.n_cta = int(n_cta);
     D.pp.err = P->err;
+    D.pp.packed = P->interval_kernel == 5 || P->interval_kernel == 0;
     return ok();
 }
 
@@ -1215,8 +1216,8 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         P->SI = opts->fft_size_interval;
     }
     if (opts) {
-        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 4)
-            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..4");
+        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 5)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..5");
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
         P->single_stream = opts->single_stream != 0;

@@ -148,7 +148,8 @@ _variant_problem = None
 
 @pytest.mark.parametrize("S", [33, 34, 36])
 @pytest.mark.parametrize("near,interval,separate", [(1, 1, 1), (2, 2, 1), (2, 1, 1), (1, 2, 1), (2, 3, 1),
-                                                    (0, 0, 0), (0, 3, 0), (0, 1, 0), (0, 4, 1)])
+                                                    (0, 0, 0), (0, 3, 0), (0, 1, 0), (0, 4, 1),
+                                                    (0, 5, 0), (0, 5, 1)])
 def test_kernel_variants_and_fft_lengths(S, near, interval, separate):
     # every product-kernel variant and interval FFT length computes the same
     # method (6^3 blocks of 16^3, 3 levels: level 2 has an interaction list)
