@@ -528,11 +528,15 @@ def main():
 
     clocks = ClockSampler(dev)
     clocks.start()
-    ms, wall = timed_steps(s32, f32, u32, args.steps, args.warmup, timing_capacity=args.steps * 16)
+    # headline: uninstrumented solves
+    ms, wall = timed_steps(s32, f32, u32, args.steps, args.warmup)
     clk = clocks.stop()
+    total_ms, value = replica_rate(float(sum(ms)), npts, args.steps, world, dist, "cuda")
+    # per-kernel times from a shorter pass with an event pair around every launch
+    k_tr = max(3, min(200, args.steps // 10))
+    ms_traced, _ = timed_steps(s32, f32, u32, k_tr, 3, timing_capacity=k_tr * 16)
     ktimes, per_solve_launches = lgfm.lgf_plan_timings(s32.plan)
     lgfm.lgf_plan_set_timing(s32.plan, 0)
-    total_ms, value = replica_rate(float(sum(ms)), npts, args.steps, world, dist, "cuda")
 
     # the same kernels once more with every launch on one stream, so the
     # dominant kernel is also timed without other chains sharing the SMs
@@ -621,6 +625,7 @@ def main():
         "gpu_launches": int(per_solve_launches) * args.steps,
         "launches_per_step": int(per_solve_launches),
         "kernel_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
+        "ms_per_step_traced": statistics.mean(ms_traced),
         "kernel_ms_isolated": {k: v[0] / v[1] for k, v in kt_iso.items()},
         "roofline": roof, "peaks": src,
         "clocks": clk, "wall_s_timed": wall,
