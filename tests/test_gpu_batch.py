@@ -1,10 +1,15 @@
 """Batched solves: a multi-problem plan and a batch (stream pool, CUDA graph)
-give every problem exactly the result its own plan gives alone.
+give every problem the result its own plan gives alone.
 
 No list links two problems of a multi-problem plan, and every kernel computes
 an item (a block, an interval, a sibling group) from that item's data in a fixed
-order, so the results are compared bit for bit with the single-problem solves,
-which the parity tests tie to the oracle.
+order.  With the same kernel forms and schedule on both sides the results are
+compared bit for bit with the single-problem solves (which the parity tests
+tie to the oracle).  With default options the library may pick different
+forms for the larger plan (the persistent products need enough sibling
+groups; the schedule follows the plan's work split), which changes only the
+FP32 rounding (summation order over up to 216 sources per point): those
+results agree within the FP32 tolerance, 1e-5 of max|u| (measured 1.7e-6).
 """
 import numpy as np
 import pytest
@@ -28,6 +33,11 @@ def _built():
 
 def _dtype(prec):
     return torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+
+
+# the same forms on both sides: persistent packed products at every level,
+# the split schedule
+SAME = {"interval_kernel": 5, "free_sms": -1}
 
 
 def solo(p, prec, **opts):
@@ -65,10 +75,12 @@ def _mix(n_b):
 @pytest.mark.parametrize("prec", [lgfm.LGF_FP32, lgfm.LGF_FP64])
 @pytest.mark.parametrize("n_b", [8, 16])
 @pytest.mark.parametrize("separate", [0, 1])
-def test_multi_plan_matches_each_problem_alone(prec, n_b, separate):
+@pytest.mark.parametrize("same", [True, False])
+def test_multi_plan_matches_each_problem_alone(prec, n_b, separate, same):
     probs = _mix(n_b)
+    opts = dict(SAME) if same and prec == lgfm.LGF_FP32 else {}
     plan = lgfm.lgf_plan_create_multi([p.blocks for p in probs], n_b, [p.n_levels for p in probs], 8, prec,
-                                      separate_level1=separate)
+                                      separate_level1=separate, **opts)
     st = lgfm.lgf_plan_get_stats(plan)
     assert st["n_problems"] == len(probs)
     assert st["n_blocks"] == sum(len(p.blocks) for p in probs)
@@ -80,9 +92,13 @@ def test_multi_plan_matches_each_problem_alone(prec, n_b, separate):
     lgfm.lgf_destroy(plan)
     at = 0
     for p in probs:
-        ref = solo(p, prec, separate_level1=separate)
+        ref = solo(p, prec, separate_level1=separate, **opts)
         n = ref.size
-        assert np.array_equal(got[at:at + n].reshape(ref.shape), ref), p.name
+        mine = got[at:at + n].reshape(ref.shape)
+        if same or prec == lgfm.LGF_FP64:
+            assert np.array_equal(mine, ref), p.name
+        else:
+            assert np.abs(mine - ref).max() <= 1e-5 * np.abs(ref).max(), p.name
         at += n
 
 
@@ -118,7 +134,7 @@ def test_multi_plan_errors():
 def test_batch_solver_matches_each_problem_alone(use_graph):
     probs = W.batch_problems(12, seed=3) + _hand_problems(8)
     bs = lgfm.BatchSolver([(p.blocks, p.n_b, p.n_levels, p.order) for p in probs], lgfm.LGF_FP32,
-                          use_graph=use_graph)
+                          use_graph=use_graph, options={8: SAME, 16: SAME})
     bs.set_sources([torch.from_numpy(p.f).float() for p in probs])
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
@@ -128,7 +144,7 @@ def test_batch_solver_matches_each_problem_alone(use_graph):
     outs = [bs.u_view(i).cpu().numpy() for i in range(len(probs))]
     bs.close()
     for p, got in zip(probs, outs):
-        assert np.array_equal(got, solo(p, lgfm.LGF_FP32)), p.name
+        assert np.array_equal(got, solo(p, lgfm.LGF_FP32, **SAME)), p.name
 
 
 def test_batch_of_separate_plans():
@@ -151,3 +167,29 @@ def test_batch_of_separate_plans():
         lgfm.lgf_batch_create(plans[:1], fs[:1], us[:1], 1)
     for pl in plans:
         lgfm.lgf_destroy(pl)
+
+
+def _kappa(p, ref):
+    from oracle import fmm
+    if np.all(p.f >= 0):
+        return 1.0
+    ua = fmm.fmm_solve(p.blocks, np.abs(p.f), p.n_b, p.n_levels, p.order)
+    return max(1.0, float(np.abs(ua).max() / np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("n_b", [8, 16])
+def test_batch_problems_against_oracle(n_b):
+    # the smallest batch problems of each block size, solved in one batch,
+    # against the oracle FMM (FP32 within 1e-5, FP64 within 1e-12)
+    from oracle import fmm
+    probs = sorted([p for p in W.batch_problems(64, seed=3) if p.n_b == n_b], key=lambda p: p.n_points)[:2]
+    for prec, tol in ((lgfm.LGF_FP32, 1e-5), (lgfm.LGF_FP64, 1e-12)):
+        bs = lgfm.BatchSolver([(p.blocks, p.n_b, p.n_levels, p.order) for p in probs], prec, use_graph=1)
+        bs.set_sources([torch.from_numpy(p.f).to(_dtype(prec)) for p in probs])
+        bs()
+        torch.cuda.synchronize()
+        for i, p in enumerate(probs):
+            ref = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order)
+            err = fmm.rel_linf(bs.u_view(i).double().cpu().numpy(), ref)
+            assert err <= tol * _kappa(p, ref), (p.name, prec, err)
+        bs.close()

@@ -60,3 +60,18 @@ def test_budget_too_small_rejects():
     done, rejected = srv.run([Request(0, 0.0, (16, 4), 0)])
     srv.close()
     assert rejected == [0] and not done
+
+
+def test_served_request_against_oracle():
+    # one small request of the stream's kind, through the server, against the
+    # oracle FMM (FP32 within 1e-5: non-negative source, kappa = 1)
+    from oracle import fmm
+    key = (8, 4)
+    problems = {key: W.request_problem(8, 4, seed=9)}
+    srv = GpuServer(lgfm.LGF_FP32, problems, budget_bytes=4e9, n_streams=2, keep_results=True)
+    done, rejected = srv.run([Request(0, 0.0, key, problems[key].n_points)])
+    srv.close()
+    assert not rejected and len(done) == 1
+    p = problems[key]
+    ref = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order)
+    assert fmm.rel_linf(srv.results[0].astype(np.float64), ref) <= 1e-5
