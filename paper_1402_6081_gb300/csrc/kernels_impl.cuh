@@ -953,17 +953,21 @@ __device__ __forceinline__ cx<float> unpack_sum(uint64_t A, uint64_t B) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(bx), "=f"(by) : "l"(B));
     return {ax - by, ay + bx};
 }
+// adj: this source group is the +x neighbour (centre row + 2) of the previous
+// pair's, whose +x coefficient plane is this pair's -x plane: carry holds it
+// and only the other 18 rows are loaded; carry returns this pair's +x plane.
 __device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
-                                                     const cx<float>* kb) {
+                                                     const cx<float>* kb, bool adj, uint64_t (&carry)[9]) {
     uint64_t kk[27];
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx)
-                kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] =
-                    *reinterpret_cast<const uint64_t*>(kb + (dx + 7 * dy + 49 * dz) * 32);
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int pl = (dy + 1) + 3 * (dz + 1);
+            kk[0 + 3 * pl] = adj ? carry[pl] : *reinterpret_cast<const uint64_t*>(kb + (-1 + 7 * dy + 49 * dz) * 32);
+            kk[1 + 3 * pl] = *reinterpret_cast<const uint64_t*>(kb + (7 * dy + 49 * dz) * 32);
+            kk[2 + 3 * pl] = *reinterpret_cast<const uint64_t*>(kb + (1 + 7 * dy + 49 * dz) * 32);
+        }
 #pragma unroll
     for (int cs = 0; cs < 8; ++cs) {
         const uint64_t fx = pk2(F[cs].x, F[cs].x), fy = pk2(F[cs].y, F[cs].y);
@@ -975,6 +979,8 @@ __device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t 
             ffma2(B[ct], fy, k);
         }
     }
+#pragma unroll
+    for (int pl = 0; pl < 9; ++pl) carry[pl] = kk[2 + 3 * pl];
 }
 
 constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
@@ -1068,9 +1074,12 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 acc[i] = czero<float>();
                 if constexpr (PACKED) A[i] = B[i] = 0ull;
             }
+            [[maybe_unused]] uint64_t carry[9];
+            int prev = -100;   // centre row of the previous pair of this group
             auto block = [&](const cx<float> (&F)[8], int centre) {
-                if constexpr (PACKED) persist_block_packed(A, B, F, sk + centre * 32);
+                if constexpr (PACKED) persist_block_packed(A, B, F, sk + centre * 32, centre == prev + 2, carry);
                 else persist_block(acc, F, sk + centre * 32);
+                prev = centre;
             };
             if (p1 > p0) {
                 cx<float> Fa[8], Fb[8];
