@@ -143,6 +143,15 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      before and after them; k > 0 = they take all but k SMs
  *                      and levels >= 2 run beside them on the rest; 0 = the
  *                      library's choice
+ *   fft_kernel         level-0 forward and inverse FFTs: 1 = one CTA per block
+ *                      (the input and output cubes through per-thread loads
+ *                      and stores); 2 = persistent, one CTA per SM taking
+ *                      blocks from a counter, the whole padded cube in shared
+ *                      memory, each block's input, spectrum and output moved
+ *                      by bulk copies that overlap the neighbouring blocks'
+ *                      passes, each line transform split into output classes
+ *                      (FP32 plans with n_b 8 or 16); 0 = 1 (the faster form
+ *                      as measured)
  * All variants compute the same sums (Eq. alg_mult); they differ only in
  * scheduling.
  */
@@ -153,7 +162,8 @@ typedef struct {
     int32_t single_stream;
     int32_t separate_level1;
     int32_t free_sms;
-    int32_t reserved[10];
+    int32_t fft_kernel;
+    int32_t reserved[9];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */
@@ -194,6 +204,7 @@ lgf_status lgf_plan_create_multi(const int32_t *block_ijk, const int64_t *block_
  *   persistent_ctas    CTAs (one per SM) of the persistent level-0 products, 0 if
  *                      that level uses another form
  *   n_levels           the largest level count of its problems
+ *   fft_kernel         the level-0 FFT form in use (see lgf_plan_options)
  */
 #define LGF_MAX_LEVELS 24
 typedef struct {
@@ -207,6 +218,7 @@ typedef struct {
     int32_t merged_level01;
     int32_t n_problems;
     int32_t persistent_ctas;
+    int32_t fft_kernel;
 } lgf_plan_stats;
 
 lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);

@@ -120,7 +120,7 @@ class lgf_plan_options(ctypes.Structure):
     _fields_ = [("fft_size_interval", ctypes.c_int32), ("near_kernel", ctypes.c_int32),
                 ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
                 ("separate_level1", ctypes.c_int32), ("free_sms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("fft_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -132,7 +132,8 @@ class lgf_plan_stats(ctypes.Structure):
                 ("groups", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32),
-                ("n_problems", ctypes.c_int32), ("persistent_ctas", ctypes.c_int32)]
+                ("n_problems", ctypes.c_int32), ("persistent_ctas", ctypes.c_int32),
+                ("fft_kernel", ctypes.c_int32)]
 
 
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
@@ -148,11 +149,13 @@ def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
 def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
                        fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
-                       single_stream: int = 0, separate_level1: int = 0, free_sms: int = 0) -> int:
+                       single_stream: int = 0, separate_level1: int = 0, free_sms: int = 0,
+                       fft_kernel: int = 0) -> int:
     """lgf_plan_create with tuning options (0 = default)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
     opts = lgf_plan_options()
     opts.free_sms = free_sms
+    opts.fft_kernel = fft_kernel
     opts.fft_size_interval = fft_size_interval
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
@@ -166,9 +169,10 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
 
 
 def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0,
-             free_sms=0):
+             free_sms=0, fft_kernel=0):
     opts = lgf_plan_options()
     opts.free_sms = free_sms
+    opts.fft_kernel = fft_kernel
     opts.fft_size_interval = fft_size_interval
     opts.near_kernel = near_kernel
     opts.interval_kernel = interval_kernel
@@ -206,7 +210,7 @@ def lgf_plan_get_stats(plan: int) -> dict:
             "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
             "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes,
             "merged_level01": st.merged_level01, "n_problems": st.n_problems,
-            "persistent_ctas": st.persistent_ctas}
+            "persistent_ctas": st.persistent_ctas, "fft_kernel": st.fft_kernel}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:
@@ -330,14 +334,15 @@ class Solver:
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
                  single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE,
-                 free_sms: int = 0):
+                 free_sms: int = 0, fft_kernel: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
         self.plan = lgf_plan_create_ex(blocks, n_b, n_levels, interp_order, precision, interp_mode,
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
                                        interval_kernel=interval_kernel, single_stream=single_stream,
-                                       separate_level1=separate_level1, free_sms=free_sms)
+                                       separate_level1=separate_level1, free_sms=free_sms,
+                                       fft_kernel=fft_kernel)
 
     @property
     def dtype(self):

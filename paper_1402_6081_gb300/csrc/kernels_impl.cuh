@@ -1135,6 +1135,395 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Level-0 transforms as persistent kernels (FP32; NIN = NOUT = S/2, S % 4 ==
+// 0).  One CTA per SM takes blocks from a counter.  Every pass splits its
+// line transforms into output classes (decimation in frequency), so all warps
+// of the CTA have work in every pass: a class-r task computes X[R m + r] of a
+// length-S line from the R input blocks of length S/R folded with W_R^{r q},
+// twisted by W_S^{r n}, and one length-S/R transform.
+//  R2C (Eq. alg_upfft): the NIN^2 input rows arrive as one tensor box while
+//  the previous block runs, 16-byte chunks swizzled per row (the tensor map's
+//  swizzle of NIN * 4 bytes), so the x pass reads whole rows without bank
+//  conflicts; x pass (two rows as one complex line, classes
+//  kx even/odd) into a row buffer; y pass (ky even/odd) into the z-input
+//  region; z pass even kz into the other region, stored by bulk copies while
+//  the odd kz are computed in place and stored in turn.  The two regions swap
+//  roles every block, so each store drains behind the next block's passes;
+//  the per-SM write path, not the arithmetic, bounds this kernel.
+//  C2R (Eq. alg_dwfft): the spectrum arrives by two bulk copies (planes NOUT
+//  and up after the z pass is done with them, the rest after the y pass);
+//  z pass in place, y pass (y even/odd) into a row buffer, x pass (x mod 4)
+//  into the output cube, which is written with the level-1 field added.
+// ctr[0] hands out blocks, ctr[1] counts CTAs that are done: the last one
+// resets both, so the next launch starts from zero.  A wait that runs out sets
+// err and ends the CTA.
+// y-pass lines per class rounded up to whole warps, so each warp has one class
+template <int S>
+__host__ __device__ constexpr int cube_ycls() {
+    return ((S / 2 + 1) * (S / 2) + 31) / 32 * 32;
+}
+template <int S>
+__host__ __device__ constexpr int cube_threads() {
+    return 2 * cube_ycls<S>() > (S / 2 + 1) * S ? 2 * cube_ycls<S>() : ((S / 2 + 1) * S + 31) / 32 * 32;
+}
+template <int S, int NIN>
+__host__ __device__ constexpr size_t r2c_cube_smem() {
+    return size_t(S) * S * (S / 2 + 1) * sizeof(cx<float>)                    // two regions of S/2 planes
+           + size_t(NIN) * NIN * ((S / 2 + 1) | 1) * sizeof(cx<float>)     // x-pass rows
+           + size_t(NIN) * NIN * NIN * sizeof(float) + 1024 + 64;           // swizzled input (1024-aligned)
+}
+template <int S, int NOUT>
+__host__ __device__ constexpr size_t c2r_cube_smem() {
+    return size_t(S) * S * (S / 2 + 1) * sizeof(cx<float>)                    // the spectrum
+           + size_t(NOUT) * NOUT * ((S / 2 + 1) | 1) * sizeof(cx<float>)   // y-pass rows
+           + size_t(NOUT) * NOUT * (NOUT | 1) * sizeof(float) + 64;         // output cube
+}
+
+// Class r of a length-S DFT with sign SIGN: out[m] = X[R m + r], m < S/R, of
+// the N inputs x (zero from N on; N a multiple of S/R).
+template <int S, int R, int r, int SIGN, int N>
+__device__ __forceinline__ void dft_class(const cx<float> (&x)[N], cx<float> (&out)[S / R]) {
+    constexpr int L = S / R;
+    static_assert(S % R == 0 && N % L == 0 && N <= S, "input blocks of length S/R");
+#pragma unroll
+    for (int n = 0; n < L; ++n) {
+        cx<float> v = x[n];
+#pragma unroll
+        for (int q = 1; q < N / L; ++q) v = v + twmul<S, SIGN>(x[n + q * L], r * q * L);
+        out[n] = twmul<S, SIGN>(v, r * n);
+    }
+    fft<S, L, SIGN, L>(out);
+}
+
+// shared -> global bulk store (both 16-byte aligned, bytes % 16 == 0) in the
+// issuing thread's current bulk group
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most N of this thread's bulk groups still reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// every bulk group of this thread complete (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// thread 0, after its last claim
+__device__ __forceinline__ void cube_done(int* ctr) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1) == int(gridDim.x) - 1) {
+        atomicExch(ctr, 0);
+        atomicExch(ctr + 1, 0);
+    }
+}
+
+// in_map: the input as rows of NIN reals (row = block * NIN^2 + z * NIN + y),
+// box NIN x NIN^2, swizzle of NIN * 4 bytes (64B for NIN = 16, 32B for 8)
+template <int S, int NIN>
+__global__ void __launch_bounds__(cube_threads<S>(), 1)
+    k_r2c_cube(const __grid_constant__ CUtensorMap in_map, const R2CItem* __restrict__ items, int n_items,
+               cx<float>* __restrict__ spec, int* __restrict__ ctr, int* __restrict__ err) {
+    constexpr int NX = S / 2 + 1, PP = S * NX, H = S / 2, NL = NIN * NIN, NP = NL / 2;
+    constexpr int RP = NX | 1, YC = cube_ycls<S>();   // x-pass row pitch (complex): odd
+    constexpr int64_t NWS = (int64_t(PP) * S + 31) / 32 * 32;
+    constexpr unsigned PLANE = PP * unsigned(sizeof(cx<float>)), ROWB = NIN * 4u, SWZ = ROWB / 16 - 1;
+    static_assert(NIN == H && S % 4 == 0 && (NIN == 16 || NIN == 8) && PP % 2 == 0,
+                  "64B or 32B swizzled rows; bulk copies move 16-byte multiples");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cx<float>* P = reinterpret_cast<cx<float>*>(smem_raw);   // [2][H planes]
+    cx<float>* XB = P + S * PP;                               // [NL rows][RP]
+    const uintptr_t xa = (reinterpret_cast<uintptr_t>(XB + NL * RP) + 1023) & ~uintptr_t(1023);
+    const unsigned char* X = reinterpret_cast<const unsigned char*>(xa);   // [NL rows][ROWB], swizzled
+    uint64_t* full = reinterpret_cast<uint64_t*>(xa + NL * ROWB);
+    int* sh = reinterpret_cast<int*>(full + 1);   // [0] next block, [1] its input landed
+    const int tid = int(threadIdx.x);
+    // The last warp has no x-pass or z-pass line: its lane 0 claims the next
+    // block during the x pass (the counter's round trip off the critical
+    // path) and fetches its rows; its lanes 0 .. H-1 each store one plane per
+    // region (own bulk groups) while the other warps compute.
+    constexpr int CLAIMER = cube_threads<S>() - 32;
+    static_assert(2 * NP <= CLAIMER && PP <= CLAIMER && H <= 32, "the last warp has no x-pass or z-pass line");
+    const bool storer = tid >= CLAIMER && tid < CLAIMER + H;
+    const int sp = tid - CLAIMER;   // plane of a storer
+    auto claim = [&] { sh[0] = atomicAdd(ctr, 1); };
+    auto load = [&] {
+        const int t = sh[0];
+        if (t < n_items) {
+            mbar_expect_tx(full, NL * ROWB);
+            tma_2d(reinterpret_cast<void*>(xa), &in_map, 0, items[t].src * NL, full);
+        }
+    };
+    // the 16-byte chunk c of row r (the swizzle XORs address bits 4.. with 7..)
+    auto xrow = [&](int r, int c) {
+        return *reinterpret_cast<const float4*>(X + r * ROWB + 16u * (unsigned(c) ^ ((unsigned(r) * ROWB >> 7) & SWZ)));
+    };
+    if (tid == 0) {
+        mbar_init(full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == CLAIMER) {
+        claim();
+        load();
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int t = sh[0];
+        if (t >= n_items) break;
+        const unsigned par = unsigned(k & 1);
+        cx<float>* Rg = P + (k & 1) * (H * PP);         // z-pass input, then odd kz
+        cx<float>* Eg = P + ((k & 1) ^ 1) * (H * PP);   // even kz
+        if (tid == 0) {
+            const bool okw = mbar_wait(full, par);
+            if (!okw) atomicExch(err, 1);
+            sh[1] = okw;
+        }
+        __syncthreads();
+        if (!sh[1]) break;
+        mbar_wait(full, par);   // complete: this thread's view of the copies
+        // x pass: rows p and p + NP as one complex line, class h = kx parity
+        if (tid < 2 * NP) {
+            const int h = tid / NP, p = tid % NP;
+            cx<float> z[H], o[H];
+#pragma unroll
+            for (int x = 0; x < NIN; x += 4) {
+                const float4 a = xrow(p, x / 4);
+                const float4 b = xrow(p + NP, x / 4);
+                z[x] = {a.x, b.x};
+                z[x + 1] = {a.y, b.y};
+                z[x + 2] = {a.z, b.z};
+                z[x + 3] = {a.w, b.w};
+            }
+            cx<float>* d0 = XB + p * RP;
+            cx<float>* d1 = XB + (p + NP) * RP;
+            // X[kx] and X[S - kx] share a class; split the two real rows
+            auto split = [&](int kx, const cx<float>& a, const cx<float>& b) {
+                d0[kx] = {0.5f * (a.x + b.x), 0.5f * (a.y - b.y)};
+                d1[kx] = {0.5f * (a.y + b.y), 0.5f * (b.x - a.x)};
+            };
+            if (h == 0) {
+                dft_class<S, 2, 0, -1>(z, o);
+#pragma unroll
+                for (int m = 0; m <= S / 4; ++m) split(2 * m, o[m], o[m == 0 ? 0 : H - m]);
+            } else {
+                dft_class<S, 2, 1, -1>(z, o);
+#pragma unroll
+                for (int m = 0; m < S / 4; ++m) split(2 * m + 1, o[m], o[H - 1 - m]);
+            }
+        }
+        if (tid == CLAIMER) claim();
+        if (storer) bulk_wait_read<1>();   // the region of the previous even kz is stored
+        __syncthreads();
+        if (tid == CLAIMER) {
+            fence_async_smem();
+            load();   // X is free
+        }
+        // y pass: lines (kx, z), class h = ky parity (whole warps), into planes z of Rg
+        if (tid % YC < NX * NIN) {
+            const int h = tid / YC, l = tid % YC, kx = l % NX, zz = l / NX;
+            cx<float> v[H], o[H];
+#pragma unroll
+            for (int y = 0; y < H; ++y) v[y] = XB[(zz * NIN + y) * RP + kx];
+            if (h == 0) dft_class<S, 2, 0, -1>(v, o);
+            else dft_class<S, 2, 1, -1>(v, o);
+            cx<float>* col = Rg + zz * PP + kx;
+#pragma unroll
+            for (int m = 0; m < H; ++m) col[(2 * m + h) * NX] = o[m];
+        }
+        if (storer) bulk_wait_read<0>();   // the region of the previous odd kz is stored
+        __syncthreads();
+        cx<float>* out = spec + int64_t(items[t].dst) * NWS;
+        // z pass, even kz = 2m into plane m of Eg
+        for (int l = tid; l < PP; l += blockDim.x) {
+            cx<float> v[H], o[H];
+#pragma unroll
+            for (int zz = 0; zz < H; ++zz) v[zz] = Rg[zz * PP + l];
+            dft_class<S, 2, 0, -1>(v, o);
+#pragma unroll
+            for (int m = 0; m < H; ++m) Eg[m * PP + l] = o[m];
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (storer) {
+            bulk_s2g(out + 2 * sp * PP, Eg + sp * PP, PLANE);
+            bulk_commit();
+        }
+        // odd kz = 2m + 1, in place over the line's own column of Rg
+        for (int l = tid; l < PP; l += blockDim.x) {
+            cx<float> v[H], o[H];
+#pragma unroll
+            for (int zz = 0; zz < H; ++zz) v[zz] = Rg[zz * PP + l];
+            dft_class<S, 2, 1, -1>(v, o);
+#pragma unroll
+            for (int m = 0; m < H; ++m) Rg[m * PP + l] = o[m];
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (storer) {
+            bulk_s2g(out + (2 * sp + 1) * PP, Rg + sp * PP, PLANE);
+            bulk_commit();
+        }
+    }
+    if (storer) bulk_wait_all();
+    __syncthreads();
+    if (tid == 0) cube_done(ctr);
+}
+
+template <int S, int NOUT>
+__global__ void __launch_bounds__(cube_threads<S>(), 1)
+    k_c2r_cube(const cx<float>* __restrict__ spec, const C2RItem* __restrict__ items, int n_items,
+               float* __restrict__ dst, int64_t dst_stride, const float* __restrict__ add, int add_n,
+               int64_t add_stride, int* __restrict__ ctr, int* __restrict__ err) {
+    constexpr int NX = S / 2 + 1, PP = S * NX, NL = NOUT * NOUT, NP = NL / 2, N3 = NOUT * NOUT * NOUT;
+    constexpr int RP = NX | 1, RS = NOUT | 1, YC = cube_ycls<S>();
+    constexpr int64_t NWS = (int64_t(PP) * S + 31) / 32 * 32;
+    constexpr unsigned PLANE = PP * unsigned(sizeof(cx<float>));
+    static_assert(NOUT == S / 2 && S % 8 == 0 && PP % 2 == 0, "bulk copies move 16-byte multiples");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cx<float>* B = reinterpret_cast<cx<float>*>(smem_raw);   // S planes
+    cx<float>* YB = B + S * PP;                               // [NL rows (z, y)][RP]
+    float* O = reinterpret_cast<float*>(YB + NL * RP);        // [NL rows][RS]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(O + NL * RS);   // [0] planes < NOUT, [1] the rest
+    int* sh = reinterpret_cast<int*>(bar + 2);                 // [0] next block, [1] its input landed
+    const int tid = int(threadIdx.x);
+    // the last warp, idle in the z pass, claims the next block then
+    constexpr int CLAIMER = cube_threads<S>() - 32;
+    static_assert(PP <= CLAIMER, "the claiming warp has no z-pass line");
+    auto load_lo = [&](int t) {
+        mbar_expect_tx(&bar[0], NOUT * PLANE);
+        bulk_g2s(B, spec + int64_t(items[t].src) * NWS, NOUT * PLANE, &bar[0]);
+    };
+    auto load_hi = [&](int t) {
+        mbar_expect_tx(&bar[1], (S - NOUT) * PLANE);
+        bulk_g2s(B + NOUT * PP, spec + int64_t(items[t].src) * NWS + NOUT * PP, (S - NOUT) * PLANE, &bar[1]);
+    };
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == CLAIMER) {
+        const int t = atomicAdd(ctr, 1);
+        sh[0] = t;
+        if (t < n_items) {
+            load_lo(t);
+            load_hi(t);
+        }
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int t = sh[0];
+        if (t >= n_items) break;
+        const unsigned par = unsigned(k & 1);
+        if (tid == 0) {
+            const bool okw = mbar_wait(&bar[0], par) && mbar_wait(&bar[1], par);
+            if (!okw) atomicExch(err, 1);
+            sh[1] = okw;
+        }
+        __syncthreads();
+        if (!sh[1]) break;
+        mbar_wait(&bar[0], par);   // complete: this thread's view of the copies
+        mbar_wait(&bar[1], par);
+        // z pass: lines (kx, ky), in place over their own column; keep z < NOUT
+        for (int l = tid; l < PP; l += blockDim.x) {
+            cx<float>* col = B + l;
+            cx<float> v[S];
+#pragma unroll
+            for (int kz = 0; kz < S; ++kz) v[kz] = col[kz * PP];
+            fft<S, S, 1, S>(v);
+#pragma unroll
+            for (int zz = 0; zz < NOUT; ++zz) col[zz * PP] = v[zz];
+        }
+        if (tid == CLAIMER) sh[0] = atomicAdd(ctr, 1);
+        __syncthreads();
+        // planes NOUT and up are free: the next block's arrive meanwhile
+        const int tn = sh[0];
+        if (tid == CLAIMER && tn < n_items) {
+            fence_async_smem();
+            load_hi(tn);
+        }
+        // y pass: lines (kx, z < NOUT), class h = y parity (whole warps), into the row buffer
+        if (tid % YC < NX * NOUT) {
+            const int h = tid / YC, l = tid % YC, kx = l % NX, zz = l / NX;
+            const cx<float>* col = B + zz * PP + kx;
+            cx<float> v[S], o[S / 2];
+#pragma unroll
+            for (int y = 0; y < S; ++y) v[y] = col[y * NX];
+            if (h == 0) dft_class<S, 2, 0, 1>(v, o);
+            else dft_class<S, 2, 1, 1>(v, o);
+#pragma unroll
+            for (int m = 0; m < NOUT / 2; ++m) YB[(zz * NOUT + 2 * m + h) * RP + kx] = o[m];
+        }
+        __syncthreads();
+        // planes below NOUT are free too
+        if (tid == CLAIMER && tn < n_items) {
+            fence_async_smem();
+            load_lo(tn);
+        }
+        // x pass: two Hermitian half-rows (rows p and p + NP) per complex
+        // inverse, class r = x mod 4
+        if (tid < 4 * NP) {
+            const int r = tid / NP, p = tid % NP;
+            const cx<float>* a = YB + p * RP;
+            const cx<float>* b = YB + (p + NP) * RP;
+            cx<float> z[S], o[S / 4];
+#pragma unroll
+            for (int kx = 0; kx < NX; ++kx) {
+                cx<float> A = a[kx], Bk = b[kx];
+                if (kx == 0 || 2 * kx == S) {   // exactly real for a real signal
+                    A.y = 0.f;
+                    Bk.y = 0.f;
+                }
+                z[kx] = {A.x - Bk.y, A.y + Bk.x};
+                if (kx > 0 && S - kx >= NX) z[S - kx] = {A.x + Bk.y, Bk.x - A.y};
+            }
+            switch (r) {
+                case 0: dft_class<S, 4, 0, 1>(z, o); break;
+                case 1: dft_class<S, 4, 1, 1>(z, o); break;
+                case 2: dft_class<S, 4, 2, 1>(z, o); break;
+                default: dft_class<S, 4, 3, 1>(z, o); break;
+            }
+#pragma unroll
+            for (int m = 0; m < NOUT / 4; ++m) {
+                O[p * RS + 4 * m + r] = o[m].x;
+                O[(p + NP) * RS + 4 * m + r] = o[m].y;
+            }
+        }
+        __syncthreads();
+        const C2RItem it = items[t];
+        float* out = dst + int64_t(it.dst) * dst_stride;
+        const float* ad = (add != nullptr && it.aux >= 0) ? add + int64_t(it.aux) * add_stride : nullptr;
+        if (NOUT % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+            for (int i = tid; i < N3 / 4; i += blockDim.x) {
+                const int x = (4 * i) % NOUT, yz = (4 * i) / NOUT;
+                float v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = O[yz * RS + x + j];
+                if (ad) {
+                    const float* q = ad + ((yz / NOUT) * add_n + yz % NOUT) * add_n + x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] += q[j];
+                }
+                reinterpret_cast<float4*>(out)[i] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        } else {
+            for (int i = tid; i < N3; i += blockDim.x) {
+                const int x = i % NOUT, yz = i / NOUT;
+                float v = O[yz * RS + x];
+                if (ad) v += ad[((yz / NOUT) * add_n + yz % NOUT) * add_n + x];
+                out[i] = v;
+            }
+        }
+    }
+    if (tid == 0) cube_done(ctr);
+}
+
+// ---------------------------------------------------------------------------
 // Reg (Eq. alg_reg) and Interp (Eq. alg_interp): tensor products of the 1D
 // matrices W[c][i][p] (weight of parent node p for child node i).  The two
 // n_I x n_I matrices travel as a by-value kernel parameter, so with every loop

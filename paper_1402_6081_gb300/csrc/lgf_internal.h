@@ -116,6 +116,19 @@ struct Launch {
                               T* u, const T* up, const T* W, int accumulate, const int* block, cudaStream_t st);
 };
 
+// Level-0 transforms as persistent kernels, FP32 (kernels_f32.cu): one CTA
+// per SM (grid from cube_fft_grid, which also sets the kernels' shared-memory
+// limit) takes blocks from the counter pair ctr[0..1] (zero between launches)
+// and moves each block's data by bulk copies; the forward transform reads its
+// input through in_map (rows of n_in reals, box n_in x n_in^2, swizzle of
+// n_in * 4 bytes).  The same transforms as Launch<float>::r2c / c2r.
+bool cube_fft_supported(int S, int n);
+cudaError_t cube_fft_grid(int S, int n, bool inverse, int n_sm, int* grid);
+cudaError_t r2c_cube(int S, int n_in, const CUtensorMap& in_map, const R2CItem* items, int n, void* spec, int grid,
+                     int* ctr, int* err, cudaStream_t st);
+cudaError_t c2r_cube(int S, int n_out, const void* spec, const C2RItem* items, int n, float* dst, int64_t ds,
+                     const float* add, int add_n, int64_t as, int grid, int* ctr, int* err, cudaStream_t st);
+
 // Reg and Interp on the tensor cores for FP32 plans (interp_tc.cu); mode is
 // an lgf_interp_mode other than NATIVE, err the plan's device error flag.
 cudaError_t interp_tc(int mode, int n_b, const int* slot, const int* parent, int n_items, float* u, const float* up,

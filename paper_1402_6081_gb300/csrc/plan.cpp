@@ -14,6 +14,7 @@
 #include <mutex>
 #include <set>
 #include <tuple>
+#include <type_traits>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -168,6 +169,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }();
     return fn;
+}
+
+// FP32 block inputs (n_blocks blocks of n^3, back to back) as rows of n reals,
+// one box per block (n x n^2 rows), 16-byte chunks swizzled within each row
+// (the row is 64 bytes for n = 16, 32 for n = 8): the persistent level-0
+// forward transform reads it
+static bool encode_rows_map(CUtensorMap* m, const float* f, int64_t n_blocks, int n) {
+    auto enc = tensor_map_encoder();
+    if (!enc || (n != 16 && n != 8) || (reinterpret_cast<uintptr_t>(f) & 15) != 0) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n_blocks) * cuuint64_t(n) * cuuint64_t(n)};
+    const cuuint64_t strides[1] = {cuuint64_t(n) * 4};
+    const cuuint32_t box[2] = {cuuint32_t(n), cuuint32_t(n * n)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(f), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           n == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // rows x NWS complex values viewed as rows x 2 NWS reals; boxes of 32
@@ -339,6 +358,15 @@ struct lgf_plan_s {
     // SMs left to the levels >= 2 chain beside the persistent level-0 products
     // (-1: none; the chain then runs before and after them)
     int free_sms = 0;
+    // level-0 transforms: 1 one CTA per block, 2 the persistent bulk-copy
+    // form (FP32); grids of the persistent form and its block counters
+    // ([0..1] forward, [2..3] inverse)
+    int fft_kernel = 0;
+    int cube_grid[2] = {0, 0};
+    int* fft_ctr = nullptr;
+    // the forward transform's input map, re-encoded when the input moves
+    CUtensorMap in_map{};
+    const void* in_map_src = nullptr;
     // levels 0 and 1 share the block grid and S0 = 2 n_b suffices for the
     // first n_b nodes of a level-1 interval: their products are summed into
     // one spectrum per block (one inverse FFT, no level-1 transforms)
@@ -960,6 +988,14 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     const bool split = Lm >= 2 && uses_persist(P, 0) && P->free_sms < 0;
     auto record = [&](int k, cudaStream_t s) { return conc ? cudaEventRecord(P->join[k], s) : cudaSuccess; };
     auto wait = [&](cudaStream_t s, int k) { return conc ? cudaStreamWaitEvent(s, P->join[k], 0) : cudaSuccess; };
+    // level-0 inverse FFT into u, plus the level-1 field add when given
+    auto c2r0 = [&](const T* add) -> cudaError_t {
+        if constexpr (std::is_same_v<T, float>)
+            if (P->fft_kernel == 2)
+                return c2r_cube(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, P->cube_grid[1],
+                                P->fft_ctr + 2, P->err, st);
+        return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
+    };
     // fork: the other chains start after all prior work on the caller's stream
     if (conc && (Lm >= 2 || (Lm >= 1 && !P->merged))) {
         LGF_CUDA(cudaEventRecord(P->fork, st));
@@ -1039,7 +1075,17 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         LGF_CUDA(record(1, s2));
     }
     // ---- level 0 on the caller's stream: forward FFT, near-field products
-    e = timed(P, "r2c_level0", st, [&] { return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st); });
+    e = timed(P, "r2c_level0", st, [&] {
+        if constexpr (std::is_same_v<T, float>)
+            if (P->fft_kernel == 2) {
+                if (P->in_map_src != f)
+                    P->in_map_src = encode_rows_map(&P->in_map, f, P->n_blocks, nb) ? f : nullptr;
+                if (P->in_map_src == f)
+                    return r2c_cube(P->S0, nb, P->in_map, lev[0].r2c, lev[0].n_r2c, lev[0].fh, P->cube_grid[0],
+                                    P->fft_ctr, P->err, st);
+            }
+        return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
     if (split) LGF_CUDA(wait(st, 1));
     if (P->merged) {
@@ -1060,9 +1106,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         LGF_CUDA(record(2, st));
         LGF_CUDA(wait(s2, 2));
         if ((r = down_part()) != LGF_OK) return r;
-        e = timed(P, "c2r_level0", st, [&] {
-            return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, nullptr, nI, n3, st);
-        });
+        e = timed(P, "c2r_level0", st, [&] { return c2r0(nullptr); });
         if (e != cudaSuccess) return cuda_fail(e, "level-0 inverse FFT");
         LGF_CUDA(record(3, st));
         LGF_CUDA(wait(s2, 3));
@@ -1127,9 +1171,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     }
     const bool has_ut1 = P->merged ? Lm >= 2 : Lm >= 1;
     const T* add = has_ut1 ? static_cast<const T*>(lev[1].ut) : nullptr;
-    e = timed(P, "c2r_level0", st, [&] {
-        return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
-    });
+    e = timed(P, "c2r_level0", st, [&] { return c2r0(add); });
     if (e != cudaSuccess) return cuda_fail(e, "level-0 inverse FFT");
     return ok();
 }
@@ -1224,6 +1266,9 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         P->merged = opts->separate_level1 == 0;
         if (opts->free_sms < -1) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: free_sms must be >= -1");
         P->free_sms = opts->free_sms;
+        if (opts->fft_kernel < 0 || opts->fft_kernel > 2)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: fft_kernel must be 0, 1 or 2");
+        P->fft_kernel = opts->fft_kernel;
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
@@ -1250,6 +1295,23 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     }
     s = build_plan(P.get(), hp);
     if (s != LGF_OK) return s;
+    {
+        const bool cube_ok = P->prec == LGF_FP32 && cube_fft_supported(P->S0, n_b);
+        if (P->fft_kernel == 2 && !cube_ok)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: fft_kernel 2 needs an FP32 plan with n_b 8 or 16");
+        // default: the per-block form (measured on GB300, 128^3 torus: 28.4 /
+        // 26.7 us forward / inverse in the step against 29.0 / 31.0 us)
+        if (P->fft_kernel == 0) P->fft_kernel = 1;
+        if (P->fft_kernel == 2) {
+            int n_sm = 0;
+            LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
+            LGF_CUDA(cube_fft_grid(P->S0, n_b, false, n_sm, &P->cube_grid[0]));
+            LGF_CUDA(cube_fft_grid(P->S0, n_b, true, n_sm, &P->cube_grid[1]));
+            void* c = nullptr;
+            if ((s = dalloc(P.get(), 4 * sizeof(int), &c, true)) != LGF_OK) return s;
+            P->fft_ctr = static_cast<int*>(c);
+        }
+    }
     for (auto& a : P->aux) LGF_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
     LGF_CUDA(cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming));
     for (auto& j : P->join) LGF_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
@@ -1301,6 +1363,7 @@ lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
     st->merged_level01 = plan->merged ? 1 : 0;
     st->n_problems = plan->n_problems;
     st->persistent_ctas = uses_persist(plan, 0) ? plan->lev[0].pp.n_cta : 0;
+    st->fft_kernel = plan->fft_kernel;
     if (plan->merged && plan->Lmac >= 1) st->nw[1] = nw_of(plan->S0);
     size_t b = 0;
     lgf_plan_workspace_bytes(plan, &b);
