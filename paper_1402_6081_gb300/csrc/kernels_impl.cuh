@@ -953,34 +953,36 @@ __device__ __forceinline__ cx<float> unpack_sum(uint64_t A, uint64_t B) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(bx), "=f"(by) : "l"(B));
     return {ax - by, ay + bx};
 }
-// adj: this source group is the +x neighbour (centre row + 2) of the previous
-// pair's, whose +x coefficient plane is this pair's -x plane: carry holds it
-// and only the other 18 rows are loaded; carry returns this pair's +x plane.
-__device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
-                                                     const cx<float>* kb, bool adj, uint64_t (&carry)[9]) {
-    uint64_t kk[27];
+// The 27 coefficients of one source group come as three x-planes of 9 (dy,
+// dz) values: plane dx holds rows centre + dx + 7 dy + 49 dz.  A source group
+// that is the +x neighbour (centre row + 2) of the previous pair's shares its
+// -x plane with that pair's +x plane.  The pair loop keeps three plane
+// register sets whose roles rotate between its two unrolled halves, so the
+// shared plane is reused in place: adjacency only skips its 9 loads.
+__device__ __forceinline__ void persist_plane(uint64_t (&P)[9], const cx<float>* kb) {
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int pl = (dy + 1) + 3 * (dz + 1);
-            kk[0 + 3 * pl] = adj ? carry[pl] : *reinterpret_cast<const uint64_t*>(kb + (-1 + 7 * dy + 49 * dz) * 32);
-            kk[1 + 3 * pl] = *reinterpret_cast<const uint64_t*>(kb + (7 * dy + 49 * dz) * 32);
-            kk[2 + 3 * pl] = *reinterpret_cast<const uint64_t*>(kb + (1 + 7 * dy + 49 * dz) * 32);
-        }
+        for (int dy = -1; dy <= 1; ++dy)
+            P[(dy + 1) + 3 * (dz + 1)] = *reinterpret_cast<const uint64_t*>(kb + (7 * dy + 49 * dz) * 32);
+}
+// the 8 x 8 sibling products of one source group from its -x, centre and +x
+// coefficient planes L, M, R
+__device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
+                                                     const uint64_t (&L)[9], const uint64_t (&M)[9],
+                                                     const uint64_t (&R)[9]) {
 #pragma unroll
     for (int cs = 0; cs < 8; ++cs) {
         const uint64_t fx = pk2(F[cs].x, F[cs].x), fy = pk2(F[cs].y, F[cs].y);
 #pragma unroll
         for (int ct = 0; ct < 8; ++ct) {
             const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
-            const uint64_t k = kk[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+            const int i = (dy + 1) + 3 * (dz + 1);
+            const uint64_t k = dx < 0 ? L[i] : dx == 0 ? M[i] : R[i];
             ffma2(A[ct], fx, k);
             ffma2(B[ct], fy, k);
         }
     }
-#pragma unroll
-    for (int pl = 0; pl < 9; ++pl) carry[pl] = kk[2 + 3 * pl];
 }
 
 constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
@@ -1074,13 +1076,11 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 acc[i] = czero<float>();
                 if constexpr (PACKED) A[i] = B[i] = 0ull;
             }
-            [[maybe_unused]] uint64_t carry[9];
+            // packed form: plane sets X, Y, Z; the first pair of an iteration
+            // takes (L, M, R) = (X, Y, Z), the second (Z, Y, X), so a +x
+            // neighbour finds its -x plane where the previous pair left its +x
+            [[maybe_unused]] uint64_t X[9], Y[9], Z[9];
             int prev = -100;   // centre row of the previous pair of this group
-            auto block = [&](const cx<float> (&F)[8], int centre) {
-                if constexpr (PACKED) persist_block_packed(A, B, F, sk + centre * 32, centre == prev + 2, carry);
-                else persist_block(acc, F, sk + centre * 32);
-                prev = centre;
-            };
             if (p1 > p0) {
                 cx<float> Fa[8], Fb[8];
                 PairSrc pa = ldg_pair(pairs + p0), pq{0, 0};
@@ -1091,14 +1091,32 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                         pq = ldg_pair(pairs + p + 1);
                         persist_load<S>(Fb, fh, pq.src, wc);
                     }
-                    block(Fa, pa.centre);
+                    if constexpr (PACKED) {
+                        const cx<float>* kb = sk + pa.centre * 32;
+                        if (pa.centre != prev + 2) persist_plane(X, kb - 32);
+                        persist_plane(Y, kb);
+                        persist_plane(Z, kb + 32);
+                        persist_block_packed(A, B, Fa, X, Y, Z);
+                        prev = pa.centre;
+                    } else {
+                        persist_block(acc, Fa, sk + pa.centre * 32);
+                    }
                     if (!hb) break;
                     const bool ha = p + 2 < p1;
                     if (ha) {
                         pa = ldg_pair(pairs + p + 2);
                         persist_load<S>(Fa, fh, pa.src, wc);
                     }
-                    block(Fb, pq.centre);
+                    if constexpr (PACKED) {
+                        const cx<float>* kb = sk + pq.centre * 32;
+                        if (pq.centre != prev + 2) persist_plane(Z, kb - 32);
+                        persist_plane(Y, kb);
+                        persist_plane(X, kb + 32);
+                        persist_block_packed(A, B, Fb, Z, Y, X);
+                        prev = pq.centre;
+                    } else {
+                        persist_block(acc, Fb, sk + pq.centre * 32);
+                    }
                     if (!ha) break;
                 }
             }
