@@ -564,19 +564,34 @@ def main():
     for _ in range(k_e2e):
         lgfm.lgf_solve_host(s32.plan, fh, uh, stream)
     e2e_serial_s = (time.perf_counter() - t0) / k_e2e
-    # pipelined: two plans on two streams, so one step's copies overlap the
-    # other's solve; every step copies its input in and its result out
-    s_b = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, fft_size_interval=args.fft_size,
-                      near_kernel=args.near_kernel, interval_kernel=args.interval_kernel, free_sms=args.free_sms)
-    lanes = [(s32, f32, u32, stream, uh), (s_b, torch.empty_like(f32), torch.empty_like(u32), torch.cuda.Stream(),
-                                           torch.empty_like(uh).pin_memory())]
+    # pipelined: one plan solving in order on its stream; each step's input
+    # copy runs ahead on an H2D stream and its result copy behind on a D2H
+    # stream, into and out of double-buffered device arrays, so the copies
+    # of neighbouring steps overlap the solve; every step still copies its
+    # input in and its result out
+    h2d_st, d2h_st = torch.cuda.Stream(), torch.cuda.Stream()
+    fds, uds = [f32, torch.empty_like(f32)], [u32, torch.empty_like(u32)]
+    uhs = [uh, torch.empty_like(uh).pin_memory()]
+    in_ready = [torch.cuda.Event() for _ in range(2)]
+    solved = [torch.cuda.Event() for _ in range(2)]
+    out_done = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_step(k):
-        sv, fd, ud, st_, uhh = lanes[k % 2]
-        with torch.cuda.stream(st_):
-            fd.copy_(fh, non_blocking=True)
-            sv(fd, ud, st_)
-            uhh.copy_(ud, non_blocking=True)
+        b = k % 2
+        with torch.cuda.stream(h2d_st):
+            if k >= 2:
+                h2d_st.wait_event(solved[b])     # the solve of step k-2 has read fds[b]
+            fds[b].copy_(fh, non_blocking=True)
+            in_ready[b].record(h2d_st)
+        stream.wait_event(in_ready[b])
+        if k >= 2:
+            stream.wait_event(out_done[b])       # step k-2's result has left uds[b]
+        s32(fds[b], uds[b], stream)
+        solved[b].record(stream)
+        with torch.cuda.stream(d2h_st):
+            d2h_st.wait_event(solved[b])
+            uhs[b].copy_(uds[b], non_blocking=True)
+            out_done[b].record(d2h_st)
 
     for k in range(4):
         e2e_step(k)
@@ -586,7 +601,6 @@ def main():
         e2e_step(k)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / k_e2e
-    s_b.close()
 
     # roofline of the dominant kernel
     dom = max(ktimes.items(), key=lambda kv: kv[1][0])
@@ -645,7 +659,8 @@ def main():
         "fp64": {"value": rate64, "unit": "points/s", "ms_per_step": statistics.mean(ms64), "steps": k64},
         "e2e": {"value": npts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(fh.numel() * 4),
                 "d2h_bytes_per_step": int(uh.numel() * 4), "steps": k_e2e,
-                "how": "two plans on two streams: pinned-host H2D copy, lgf_solve, D2H copy every step; "
+                "how": "one plan solving in order; every step's pinned-host H2D copy runs ahead on a copy stream "
+                       "and its D2H copy behind on another, double-buffered device arrays; "
                        "wall clock over all steps"},
         "e2e_serial": {"value": npts / e2e_serial_s, "unit": "points/s",
                        "how": "lgf_solve_host per step (copy in, solve, copy out, synchronize)"},
