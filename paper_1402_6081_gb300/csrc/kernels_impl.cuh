@@ -985,6 +985,19 @@ __device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t 
     }
 }
 
+// Store of a product spectrum value with an L2 evict-last policy: the level-0
+// inverse FFT reads these spectra right after the launch, and the launch's own
+// traffic (source spectra, coefficient chunks) would otherwise push them out.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_keep(cx<float>* p, cx<float> v, uint64_t policy) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy)
+                 : "memory");
+}
+
 constexpr unsigned kPersistBuf = 343u * 32u * sizeof(cx<float>);   // bytes per coefficient buffer
 constexpr unsigned kPersistFill = unsigned(kSymRows) * 32u * sizeof(cx<float>);   // bytes copied per chunk
 constexpr size_t kPersistSmem = 2 * size_t(kPersistBuf) + 64;
@@ -1007,6 +1020,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
     if (u0 >= u1) return;
     const long long c0 = u0 / n_groups, c1 = (u1 - 1) / n_groups;
     const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    const uint64_t keep = l2_evict_last_policy();
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -1127,7 +1141,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
             if (w < NW) {
                 cx<float>* out = uh + int64_t(__ldg(order + pos)) * (8 * NWS) + w;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) out[i * NWS] = acc[i];
+                for (int i = 0; i < 8; ++i) st_keep(out + i * NWS, acc[i], keep);
             }
         }
         // this warp is done with chunk c; the last one out refills the buffer
