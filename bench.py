@@ -294,8 +294,8 @@ def irregular_run(torch, lgfm, steps: int, flush):
     the FP64 oracle at 1e-12 on the other configs)."""
     p = W.tori_irregular(2)
     stream = torch.cuda.Stream()
-    modes = {"fp32": lgfm.LGF_INTERP_NATIVE, "bf16": lgfm.LGF_INTERP_BF16, "fp16": lgfm.LGF_INTERP_FP16,
-             "bf16x3": lgfm.LGF_INTERP_BF16X3}
+    modes = {"fp32": lgfm.LGF_INTERP_NATIVE, "fp32_compensated": lgfm.LGF_INTERP_COMPENSATED,
+             "bf16": lgfm.LGF_INTERP_BF16, "fp16": lgfm.LGF_INTERP_FP16, "bf16x3": lgfm.LGF_INTERP_BF16X3}
 
     def run(prec, mode, k):
         dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32

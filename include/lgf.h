@@ -66,12 +66,23 @@ typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
  *   LGF_INTERP_FP16    FP16 inputs (11-bit significand; magnitudes above
  *                      65504 overflow: fields of order 1e4 or more need NATIVE)
  *   LGF_INTERP_BF16X3  inputs split into three BF16 parts, six partial
- *                      products: close to FP32 accuracy */
+ *                      products: close to FP32 accuracy
+ * and, on the CUDA cores:
+ *   LGF_INTERP_COMPENSATED  FP32 passes whose dot products carry the exact
+ *                      rounding error of every product and sum (FMA-based
+ *                      TwoProduct and TwoSum, accumulated as in Ogita, Rump
+ *                      and Oishi's Dot2): each pass's output is its sum in
+ *                      twice the working precision, rounded once.  Several
+ *                      times the arithmetic of NATIVE in these small kernels;
+ *                      for deep FP32 trees where the interpolation passes'
+ *                      roundings, amplified by the stencil, approach the
+ *                      tolerance */
 typedef enum {
     LGF_INTERP_NATIVE = 0,
     LGF_INTERP_BF16 = 1,
     LGF_INTERP_FP16 = 2,
-    LGF_INTERP_BF16X3 = 3
+    LGF_INTERP_BF16X3 = 3,
+    LGF_INTERP_COMPENSATED = 4
 } lgf_interp_mode;
 
 /*
@@ -92,8 +103,8 @@ typedef enum {
  *   precision     LGF_FP32 or LGF_FP64 (FFTs, products and interpolation);
  *                 the LGF values and spectra are always generated in FP64
  *   interp_mode   LGF_INTERP_NATIVE, or for FP32 plans LGF_INTERP_BF16,
- *                 LGF_INTERP_FP16, LGF_INTERP_BF16X3 (LGF_ERR_UNSUPPORTED for
- *                 FP64 plans)
+ *                 LGF_INTERP_FP16, LGF_INTERP_BF16X3, LGF_INTERP_COMPENSATED
+ *                 (LGF_ERR_UNSUPPORTED for FP64 plans)
  *   out           receives the plan
  *
  * Runs on the host plus uploads on the current device; synchronous.

@@ -21,6 +21,7 @@ LGF_INTERP_NATIVE = 0
 LGF_INTERP_BF16 = 1
 LGF_INTERP_FP16 = 2
 LGF_INTERP_BF16X3 = 3
+LGF_INTERP_COMPENSATED = 4
 
 _STATUS = {0: "LGF_OK", 1: "LGF_ERR_INVALID_ARG", 2: "LGF_ERR_UNSUPPORTED", 3: "LGF_ERR_OOM",
            4: "LGF_ERR_CUDA", 5: "LGF_ERR_TIMEOUT", 6: "LGF_ERR_BUDGET"}

@@ -1567,12 +1567,42 @@ struct InterpW {
     T w[2][NI][NI];
 };
 
+// Products over the support of each row only (NMAX > 0; interp_lo/len give
+// it at compile time after unrolling): the same FMAs in the same order as the
+// dense loops minus those with a zero weight, so the same bits.
+template <typename T, int NI, int NMAX, int C>
+__device__ __forceinline__ void apply_wt_sp(const InterpW<T, NI>& W, const T (&in)[NI], T (&out)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int lo = interp_lo(NI - 1, NMAX, C, i), len = interp_len(NI - 1, NMAX, C, i);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < len) out[lo + k] = fma(W.w[C][i][lo + k], in[i], out[lo + k]);
+    }
+}
+template <typename T, int NI, int NMAX, int C>
+__device__ __forceinline__ void apply_w_sp(const InterpW<T, NI>& W, const T (&in)[NI], T (&out)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int lo = interp_lo(NI - 1, NMAX, C, i), len = interp_len(NI - 1, NMAX, C, i);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < len) out[i] = fma(W.w[C][i][lo + k], in[lo + k], out[i]);
+    }
+}
+
 // out[p] = sum_i W[c][i][p] in[i]   (adjoint: child line -> parent line).
-// c is uniform over the CTA; each branch is a fully unrolled dense product.
-template <typename T, int NI>
+// c is uniform over the CTA; each branch is a fully unrolled dense product
+// (NMAX = 0) or a product over the rows' supports.
+template <typename T, int NI, int NMAX = 0>
 __device__ __forceinline__ void apply_wt(const InterpW<T, NI>& W, int c, const T (&in)[NI], T (&out)[NI]) {
 #pragma unroll
     for (int p = 0; p < NI; ++p) out[p] = T(0);
+    if constexpr (NMAX > 0) {
+        if (c == 0) apply_wt_sp<T, NI, NMAX, 0>(W, in, out);
+        else apply_wt_sp<T, NI, NMAX, 1>(W, in, out);
+        return;
+    }
     if (c == 0) {
 #pragma unroll
         for (int i = 0; i < NI; ++i)
@@ -1587,10 +1617,15 @@ __device__ __forceinline__ void apply_wt(const InterpW<T, NI>& W, int c, const T
 }
 
 // out[i] = sum_p W[c][i][p] in[p]   (interpolation: parent line -> child line)
-template <typename T, int NI>
+template <typename T, int NI, int NMAX = 0>
 __device__ __forceinline__ void apply_w(const InterpW<T, NI>& W, int c, const T (&in)[NI], T (&out)[NI]) {
 #pragma unroll
     for (int i = 0; i < NI; ++i) out[i] = T(0);
+    if constexpr (NMAX > 0) {
+        if (c == 0) apply_w_sp<T, NI, NMAX, 0>(W, in, out);
+        else apply_w_sp<T, NI, NMAX, 1>(W, in, out);
+        return;
+    }
     if (c == 0) {
 #pragma unroll
         for (int i = 0; i < NI; ++i)
@@ -1604,6 +1639,123 @@ __device__ __forceinline__ void apply_w(const InterpW<T, NI>& W, int c, const T 
     }
 }
 
+// Compensated form of the two products above (FP32, interpolation mode
+// COMPENSATED).  TwoProduct (an FMA gives the exact error of w * x) and
+// TwoSum (Knuth: the exact error of s + p in six additions) are error-free
+// transformations; adding every error into e (Ogita, Rump and Oishi's Dot2)
+// leaves s + e equal to the dot product summed in twice the working
+// precision.  The __f*_rn intrinsics are never contracted or reassociated.
+// Zero weights (outside the n_max-node window) are skipped.
+__device__ __forceinline__ void acc_comp(float& s, float& e, float w, float x) {
+    if (w == 0.f) return;
+    const float p = __fmul_rn(w, x);
+    const float pe = __fmaf_rn(w, x, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(te, pe));
+}
+template <int NI, int NMAX, int C>
+__device__ __forceinline__ void apply_wt_comp_sp(const InterpW<float, NI>& W, const float (&in)[NI], float (&s)[NI],
+                                                 float (&e)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int lo = interp_lo(NI - 1, NMAX, C, i), len = interp_len(NI - 1, NMAX, C, i);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < len) acc_comp(s[lo + k], e[lo + k], W.w[C][i][lo + k], in[i]);
+    }
+}
+template <int NI, int NMAX, int C>
+__device__ __forceinline__ void apply_w_comp_sp(const InterpW<float, NI>& W, const float (&in)[NI], float (&s)[NI],
+                                                float (&e)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int lo = interp_lo(NI - 1, NMAX, C, i), len = interp_len(NI - 1, NMAX, C, i);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < len) acc_comp(s[i], e[i], W.w[C][i][lo + k], in[lo + k]);
+    }
+}
+// (s, e)[p] += sum_i W[c][i][p] in[i]
+template <int NI, int NMAX = 0>
+__device__ __forceinline__ void apply_wt_comp(const InterpW<float, NI>& W, int c, const float (&in)[NI],
+                                              float (&s)[NI], float (&e)[NI]) {
+    if constexpr (NMAX > 0) {
+        if (c == 0) apply_wt_comp_sp<NI, NMAX, 0>(W, in, s, e);
+        else apply_wt_comp_sp<NI, NMAX, 1>(W, in, s, e);
+        return;
+    }
+    if (c == 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) acc_comp(s[p], e[p], W.w[0][i][p], in[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) acc_comp(s[p], e[p], W.w[1][i][p], in[i]);
+    }
+}
+// (s, e)[i] += sum_p W[c][i][p] in[p]
+template <int NI, int NMAX = 0>
+__device__ __forceinline__ void apply_w_comp(const InterpW<float, NI>& W, int c, const float (&in)[NI],
+                                             float (&s)[NI], float (&e)[NI]) {
+    if constexpr (NMAX > 0) {
+        if (c == 0) apply_w_comp_sp<NI, NMAX, 0>(W, in, s, e);
+        else apply_w_comp_sp<NI, NMAX, 1>(W, in, s, e);
+        return;
+    }
+    if (c == 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) acc_comp(s[i], e[i], W.w[0][i][p], in[p]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int p = 0; p < NI; ++p) acc_comp(s[i], e[i], W.w[1][i][p], in[p]);
+    }
+}
+
+// One pass of a line: out = sum over the given children of the adjoint (Reg)
+// products, plain or compensated.
+template <typename T, int NI, bool COMP, int NMAX>
+struct LineSum {
+    T s[NI], e[NI];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int p = 0; p < NI; ++p) s[p] = e[p] = T(0);
+    }
+    __device__ __forceinline__ void add_wt(const InterpW<T, NI>& W, int c, const T (&in)[NI]) {
+        if constexpr (COMP) {
+            apply_wt_comp<NI, NMAX>(W, c, in, s, e);
+        } else {
+            T o[NI];
+            apply_wt<T, NI, NMAX>(W, c, in, o);
+#pragma unroll
+            for (int p = 0; p < NI; ++p) s[p] += o[p];
+        }
+    }
+    __device__ __forceinline__ void add_w(const InterpW<T, NI>& W, int c, const T (&in)[NI]) {
+        if constexpr (COMP) {
+            apply_w_comp<NI, NMAX>(W, c, in, s, e);
+        } else {
+            T o[NI];
+            apply_w<T, NI, NMAX>(W, c, in, o);
+#pragma unroll
+            for (int p = 0; p < NI; ++p) s[p] += o[p];
+        }
+    }
+    __device__ __forceinline__ T get(int p) const {
+        if constexpr (COMP) return __fadd_rn(s[p], e[p]);
+        else return s[p];
+    }
+};
+
 constexpr int kLineThreads = 320;   // >= 17*17 lines of a pass
 
 // Reg: one CTA per parent interval; the parent's sources accumulate in the
@@ -1611,7 +1763,7 @@ constexpr int kLineThreads = 320;   // >= 17*17 lines of a pass
 // block: its sources occupy nodes [0, n_b)^3 and its last node plane is 0.
 // One shared buffer: every pass reads its whole line into registers, then a
 // barrier, then writes.
-template <typename T, int NI>
+template <typename T, int NI, int NMAX = 0>
 __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ child_src, int child_is_block,
                                                       const int* __restrict__ child_index,
                                                       const int* __restrict__ parent_slot,
@@ -1641,7 +1793,7 @@ __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ chil
 #pragma unroll
                 for (int x = 0; x < NI; ++x) in[x] = row[x];
             }
-            apply_wt(W, cxp, in, out);
+            apply_wt<T, NI, NMAX>(W, cxp, in, out);
         }
         __syncthreads();                                      // previous child's z pass is done with a
         if (act) {
@@ -1654,7 +1806,7 @@ __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ chil
             const int p = t % NI, z = t / NI;
 #pragma unroll
             for (int y = 0; y < NI; ++y) in[y] = a[(z * NI + y) * NI + p];
-            apply_wt(W, cyp, in, out);
+            apply_wt<T, NI, NMAX>(W, cyp, in, out);
         }
         __syncthreads();
         if (act) {
@@ -1667,7 +1819,7 @@ __global__ void __launch_bounds__(kLineThreads) k_reg(const T* __restrict__ chil
         if (act) {
 #pragma unroll
             for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
-            apply_wt(W, czp, in, out);
+            apply_wt<T, NI, NMAX>(W, czp, in, out);
 #pragma unroll
             for (int r = 0; r < NI; ++r) acc[r] += out[r];
         }
@@ -1693,7 +1845,7 @@ constexpr int kRegThreads = 768;   // >= 2 * 17 * 17 (one y-pass item per thread
 template <typename T, int NI>
 __host__ __device__ constexpr size_t reg_wide_smem() { return sizeof(T) * 4 * size_t(NI) * NI * NI; }
 
-template <typename T, int NI>
+template <typename T, int NI, bool COMP = false, int NMAX = 0>
 __global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ child_src, int child_is_block,
                                                           const int* __restrict__ child_index,
                                                           const int* __restrict__ parent_slot,
@@ -1705,14 +1857,13 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ 
     // z pass (4 N2 items, a thread may take two)
     for (int it = t; it < 4 * N2; it += kRegThreads) {
         const int x = it % NI, y = (it / NI) % NI, cxy = it / N2;
-        T out[NI];
-#pragma unroll
-        for (int p = 0; p < NI; ++p) out[p] = T(0);
+        LineSum<T, NI, COMP, NMAX> out;
+        out.zero();
 #pragma unroll
         for (int cz = 0; cz < 2; ++cz) {
             const int s = __ldg(child_index + blockIdx.x * 8 + cxy + 4 * cz);
             if (s < 0) continue;
-            T in[NI], o[NI];
+            T in[NI];
             if (child_is_block) {
                 const bool live = x < NB && y < NB;
                 const T* col = child_src + int64_t(s) * NB * NB * NB + y * NB + x;
@@ -1723,61 +1874,53 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ 
 #pragma unroll
                 for (int z = 0; z < NI; ++z) in[z] = __ldg(col + z * N2);
             }
-            apply_wt(W, cz, in, o);
-#pragma unroll
-            for (int p = 0; p < NI; ++p) out[p] += o[p];
+            out.add_wt(W, cz, in);
         }
 #pragma unroll
-        for (int p = 0; p < NI; ++p) a[(cxy * NI + p) * N2 + y * NI + x] = out[p];
+        for (int p = 0; p < NI; ++p) a[(cxy * NI + p) * N2 + y * NI + x] = out.get(p);
     }
     __syncthreads();
     // y pass: 2 N2 items (cx, pz, x) <= kRegThreads, b[cx][pz][py][x] over a
-    T yout[NI];
+    LineSum<T, NI, COMP, NMAX> yout;
     const bool ya = t < 2 * N2;
     if (ya) {
         const int x = t % NI, pz = (t / NI) % NI, cx = t / N2;
-#pragma unroll
-        for (int p = 0; p < NI; ++p) yout[p] = T(0);
+        yout.zero();
 #pragma unroll
         for (int cy = 0; cy < 2; ++cy) {
-            T in[NI], o[NI];
+            T in[NI];
             const T* col = a + ((cx + 2 * cy) * NI + pz) * N2 + x;
 #pragma unroll
             for (int y = 0; y < NI; ++y) in[y] = col[y * NI];
-            apply_wt(W, cy, in, o);
-#pragma unroll
-            for (int p = 0; p < NI; ++p) yout[p] += o[p];
+            yout.add_wt(W, cy, in);
         }
     }
     __syncthreads();
     if (ya) {
         const int x = t % NI, pz = (t / NI) % NI, cx = t / N2;
 #pragma unroll
-        for (int p = 0; p < NI; ++p) a[((cx * NI + pz) * NI + p) * NI + x] = yout[p];
+        for (int p = 0; p < NI; ++p) a[((cx * NI + pz) * NI + p) * NI + x] = yout.get(p);
     }
     __syncthreads();
     // x pass: N2 items (pz, py); rows staged in a, then stored coalesced
-    T xout[NI];
+    LineSum<T, NI, COMP, NMAX> xout;
     const bool xa = t < N2;
     if (xa) {
         const int py = t % NI, pz = t / NI;
-#pragma unroll
-        for (int p = 0; p < NI; ++p) xout[p] = T(0);
+        xout.zero();
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) {
-            T in[NI], o[NI];
+            T in[NI];
             const T* row = a + ((cx * NI + pz) * NI + py) * NI;
 #pragma unroll
             for (int x = 0; x < NI; ++x) in[x] = row[x];
-            apply_wt(W, cx, in, o);
-#pragma unroll
-            for (int p = 0; p < NI; ++p) xout[p] += o[p];
+            xout.add_wt(W, cx, in);
         }
     }
     __syncthreads();
     if (xa) {
 #pragma unroll
-        for (int p = 0; p < NI; ++p) a[t * NI + p] = xout[p];
+        for (int p = 0; p < NI; ++p) a[t * NI + p] = xout.get(p);
     }
     __syncthreads();
     T* o = dst + int64_t(__ldg(parent_slot + blockIdx.x)) * N3;
@@ -1787,7 +1930,7 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ 
 // Interp: u[slot] += (W_cz x W_cy x W_cx) up[parent], c = slot & 7.
 // With block != nullptr the output is the child's first NI-1 nodes per axis,
 // added into u at block[i] * (NI-1)^3 (a level-1 interval's block points).
-template <typename T, int NI>
+template <typename T, int NI, bool COMP = false, int NMAX = 0>
 __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__ slot,
                                                          const int* __restrict__ parent, T* __restrict__ u,
                                                          const T* __restrict__ up, const InterpW<T, NI> W,
@@ -1800,11 +1943,19 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
     const int c = s & 7, cxp = c & 1, cyp = (c >> 1) & 1, czp = c >> 2;
     const T* U = up + int64_t(parent[blockIdx.x]) * N3;
     T in[NI], out[NI];
+    // one line through W_c: plain or compensated sums
+    auto line = [&](int cc) {
+        LineSum<T, NI, COMP, NMAX> sum;
+        sum.zero();
+        sum.add_w(W, cc, in);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) out[i] = sum.get(i);
+    };
     // x pass: line (pz, py) -> a[pz][py][ix]
     if (act) {
 #pragma unroll
         for (int x = 0; x < NI; ++x) in[x] = U[t * NI + x];
-        apply_w(W, cxp, in, out);
+        line(cxp);
 #pragma unroll
         for (int x = 0; x < NI; ++x) a[t * NI + x] = out[x];
     }
@@ -1814,7 +1965,7 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
         const int ix = t % NI, z = t / NI;
 #pragma unroll
         for (int y = 0; y < NI; ++y) in[y] = a[(z * NI + y) * NI + ix];
-        apply_w(W, cyp, in, out);
+        line(cyp);
     }
     __syncthreads();
     if (act) {
@@ -1827,7 +1978,7 @@ __global__ void __launch_bounds__(kLineThreads) k_interp(const int* __restrict__
     if (act) {
 #pragma unroll
         for (int z = 0; z < NI; ++z) in[z] = a[z * N2 + t];
-        apply_w(W, czp, in, out);
+        line(czp);
         if (block) {
             constexpr int NB = NI - 1;
             const int ix = t % NI, iy = t / NI;
@@ -2053,43 +2204,54 @@ static dev::InterpW<T, NI> pack_w(const T* W) {
     return p;
 }
 
-// W here is the host copy of the 2 x n_I x n_I matrices (plan precision).
-template <typename T>
-cudaError_t Launch<T>::reg(int n_b, int /*n_max*/, const T* child_src, int child_is_block,
-                           const int* child_index, const int* parent_slot, int n_parents, T* dst,
-                           const T* W, cudaStream_t st) {
-    if (n_parents == 0) return cudaSuccess;
-#define LGF_REG(NI)                                                                                     \
-    if (n_b + 1 == NI && sizeof(T) == 8) {                                                              \
-        dev::k_reg<T, NI><<<n_parents, dev::kLineThreads, 0, st>>>(child_src, child_is_block, child_index, \
-                                                                  parent_slot, dst, pack_w<T, NI>(W));  \
-        return cudaGetLastError();                                                                      \
-    }                                                                                                   \
-    if (n_b + 1 == NI) {                                                                                \
-        constexpr size_t smem = dev::reg_wide_smem<T, NI>();                                           \
-        auto kern = dev::k_reg_wide<T, NI>;                                                             \
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-        if (e != cudaSuccess) return e;                                                                 \
-        kern<<<n_parents, dev::kRegThreads, smem, st>>>(child_src, child_is_block, child_index, parent_slot, \
-                                                        dst, pack_w<T, NI>(W));                         \
-        return cudaGetLastError();                                                                      \
+template <typename T, int NI, int NMAX>
+static cudaError_t launch_reg(const T* child_src, int child_is_block, const int* child_index, const int* parent_slot,
+                              int n_parents, T* dst, const T* W, int comp, cudaStream_t st) {
+    if constexpr (sizeof(T) == 8) {
+        dev::k_reg<T, NI, NMAX><<<n_parents, dev::kLineThreads, 0, st>>>(child_src, child_is_block, child_index,
+                                                                        parent_slot, dst, pack_w<T, NI>(W));
+        return cudaGetLastError();
+    } else {
+        constexpr size_t smem = dev::reg_wide_smem<T, NI>();
+        auto kern = comp ? dev::k_reg_wide<T, NI, true, NMAX> : dev::k_reg_wide<T, NI, false, NMAX>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<n_parents, dev::kRegThreads, smem, st>>>(child_src, child_is_block, child_index, parent_slot, dst,
+                                                        pack_w<T, NI>(W));
+        return cudaGetLastError();
     }
-    LGF_REG(5) LGF_REG(9) LGF_REG(17)
+}
+
+// W here is the host copy of the 2 x n_I x n_I matrices (plan precision).
+// Stencils with a supported n_max run over each row's support only.
+template <typename T>
+cudaError_t Launch<T>::reg(int n_b, int n_max, const T* child_src, int child_is_block,
+                           const int* child_index, const int* parent_slot, int n_parents, T* dst,
+                           const T* W, int comp, cudaStream_t st) {
+    if (n_parents == 0) return cudaSuccess;
+    const int nm = interp_sparse(n_b, n_max) ? n_max : 0;
+#define LGF_REG(NI, NM)                                                                                       \
+    if (n_b + 1 == NI && nm == NM)                                                                            \
+        return launch_reg<T, NI, NM>(child_src, child_is_block, child_index, parent_slot, n_parents, dst, W, comp, st);
+    LGF_REG(5, 0) LGF_REG(9, 0) LGF_REG(9, 7) LGF_REG(9, 9) LGF_REG(17, 0) LGF_REG(17, 7) LGF_REG(17, 9)
 #undef LGF_REG
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t Launch<T>::interp(int n_b, const int* slot, const int* parent, int n_items, T* u,
-                              const T* up, const T* W, int accumulate, const int* block, cudaStream_t st) {
+cudaError_t Launch<T>::interp(int n_b, int n_max, const int* slot, const int* parent, int n_items, T* u,
+                              const T* up, const T* W, int accumulate, const int* block, int comp,
+                              cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-#define LGF_INTERP(NI)                                                                                      \
-    if (n_b + 1 == NI) {                                                                                    \
-        dev::k_interp<T, NI><<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W),    \
-                                                                   accumulate, block);                     \
-        return cudaGetLastError();                                                                          \
+    const int nm = interp_sparse(n_b, n_max) ? n_max : 0;
+#define LGF_INTERP(NI, NM)                                                                                    \
+    if (n_b + 1 == NI && nm == NM) {                                                                          \
+        auto kern = comp ? dev::k_interp<T, NI, sizeof(T) == 4, NM> : dev::k_interp<T, NI, false, NM>;          \
+        kern<<<n_items, dev::kLineThreads, 0, st>>>(slot, parent, u, up, pack_w<T, NI>(W), accumulate, block); \
+        return cudaGetLastError();                                                                            \
     }
-    LGF_INTERP(5) LGF_INTERP(9) LGF_INTERP(17)
+    LGF_INTERP(5, 0) LGF_INTERP(9, 0) LGF_INTERP(9, 7) LGF_INTERP(9, 9) LGF_INTERP(17, 0) LGF_INTERP(17, 7)
+    LGF_INTERP(17, 9)
 #undef LGF_INTERP
     return cudaErrorInvalidValue;
 }

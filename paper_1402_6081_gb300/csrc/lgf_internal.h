@@ -45,6 +45,29 @@ int plan_timing_capacity(const lgf_plan_s* plan);
 // W[c][i][p] (2 x n_I x n_I) for child c node i and parent node p.
 std::vector<double> interp_weights(int n_b, int n_max);
 
+#if defined(__CUDACC__)
+#define LGF_HD __host__ __device__
+#else
+#define LGF_HD
+#endif
+// Support of row i of W[c] (Sec. 2.5 stencil): child c node i sits at parent
+// coordinate x = c n_b / 2 + i / 2.  An integer x is a parent node (one
+// weight, 1); otherwise x = k + 1/2 takes the n_max nodes nearest it, the odd
+// extra node on the side of the interval centre n_b / 2 (the lower side at the
+// centre), shifted inside [0, n_b].  First node and count; interp_weights
+// fills exactly these entries and the kernels sum only over them.
+LGF_HD constexpr int interp_lo(int n_b, int n_max, int c, int i) {
+    const int twice = c * n_b + i;   // 2x
+    if (twice % 2 == 0) return twice / 2;
+    const int k = twice / 2;
+    const int lo = n_max % 2 == 0 ? k - n_max / 2 + 1 : (twice < n_b ? k - (n_max - 1) / 2 + 1 : k - (n_max - 1) / 2);
+    const int top = n_b + 1 - n_max;
+    return lo < 0 ? 0 : lo > top ? top : lo;
+}
+LGF_HD constexpr int interp_len(int n_b, int n_max, int c, int i) { return (c * n_b + i) % 2 == 0 ? 1 : n_max; }
+// n_max values with support-only Reg/Interp kernels (others: dense loops)
+LGF_HD constexpr bool interp_sparse(int n_b, int n_max) { return (n_b == 8 || n_b == 16) && (n_max == 7 || n_max == 9); }
+
 // ---- FFT sizes ----
 // Level 0 pads a block of n_b to S0 = 2 n_b per axis; levels >= 1 pad an
 // interval of n_I = n_b + 1 nodes to S_I (>= 2 n_I - 1).  R2C keeps
@@ -107,13 +130,15 @@ struct Launch {
     static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
                                    cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
+    // comp (FP32): compensated sums (interpolation mode COMPENSATED).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,
                            const int* child_index, const int* parent_slot, int n_parents,
-                           T* dst, const T* W, cudaStream_t st);
+                           T* dst, const T* W, int comp, cudaStream_t st);
     // u[slot] (+)= Interp(u_parent[parent]) for each item (accumulate: add, else
     // store); with block != nullptr: u[block[i]] += the first n_b nodes per axis.
-    static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items,
-                              T* u, const T* up, const T* W, int accumulate, const int* block, cudaStream_t st);
+    static cudaError_t interp(int n_b, int n_max, const int* slot, const int* parent, int n_items,
+                              T* u, const T* up, const T* W, int accumulate, const int* block, int comp,
+                              cudaStream_t st);
 };
 
 // Level-0 transforms as persistent kernels, FP32 (kernels_f32.cu): one CTA

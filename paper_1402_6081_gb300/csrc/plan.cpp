@@ -73,15 +73,7 @@ std::vector<double> interp_weights(int n_b, int n_max) {
                 continue;
             }
             const double x = 0.5 * twice;
-            const int k = twice / 2;   // floor(x), x = k + 1/2
-            int lo;
-            if (n_max % 2 == 0) {
-                lo = k - n_max / 2 + 1;
-            } else {
-                const int m = (n_max - 1) / 2;
-                lo = (twice < n_b) ? k - m + 1 : k - m;   // twice < n_b  <=>  x < centre
-            }
-            lo = std::max(0, std::min(lo, nI - n_max));
+            const int lo = interp_lo(n_b, n_max, c, i);
             for (int a = lo; a < lo + n_max; ++a) {
                 double w = 1.0;
                 for (int b = lo; b < lo + n_max; ++b)
@@ -1002,14 +994,18 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if (!P->merged) LGF_CUDA(cudaStreamWaitEvent(s1, P->fork, 0));
         if (Lm >= 2) LGF_CUDA(cudaStreamWaitEvent(s2, P->fork, 0));
     }
+    // Reg/Interp arithmetic: tensor-core modes, or the CUDA-core kernels with
+    // plain or compensated sums
+    const bool tc_mode = P->interp_mode != LGF_INTERP_NATIVE && P->interp_mode != LGF_INTERP_COMPENSATED;
+    const int comp = P->interp_mode == LGF_INTERP_COMPENSATED ? 1 : 0;
     // Interp of level l + 1 into the level-l items of D (see Launch::interp)
     auto interp = [&](DevLevel& D, T* out, const T* up, int accumulate, const int* block, cudaStream_t s) {
         if constexpr (sizeof(T) == 4) {
-            if (P->interp_mode != LGF_INTERP_NATIVE)
+            if (tc_mode)
                 return interp_tc(P->interp_mode, nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block,
                                  P->err, s);
         }
-        return Lc::interp(nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block, s);
+        return Lc::interp(nb, P->n_max, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block, comp, s);
     };
     // ---- levels >= 2 upward on s2: Reg from the level below, forward FFT
     auto up_part = [&]() -> lgf_status {
@@ -1019,12 +1015,12 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "reg", s2, [&] {
                 const T* src = from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft);
                 if constexpr (sizeof(T) == 4) {
-                    if (P->interp_mode != LGF_INTERP_NATIVE)
+                    if (tc_mode)
                         return reg_tc(P->interp_mode, nb, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
                                       static_cast<T*>(D.ft), W, P->err, s2);
                 }
                 return Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
-                               static_cast<T*>(D.ft), W, s2);
+                               static_cast<T*>(D.ft), W, comp, s2);
             });
             if (e != cudaSuccess) return cuda_fail(e, "regularization");
             if (D.m2l) {
@@ -1233,8 +1229,8 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: precision must be LGF_FP32 or LGF_FP64");
-    if (interp_mode < LGF_INTERP_NATIVE || interp_mode > LGF_INTERP_BF16X3)
-        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..3");
+    if (interp_mode < LGF_INTERP_NATIVE || interp_mode > LGF_INTERP_COMPENSATED)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..4");
     if (interp_mode != LGF_INTERP_NATIVE && precision != LGF_FP32)
         return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: reduced-precision interpolation modes need an FP32 plan");
     auto P = std::make_unique<lgf_plan_s>();

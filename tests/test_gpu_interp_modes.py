@@ -9,7 +9,9 @@ through up to 12 such roundings (3 Reg + 3 Interp passes at each of two
 levels in these 4-level trees), each amplified by the Lebesgue constant of the
 order-8 stencil (about 3), so |error| <= 36 u of the far field, which is below
 max|u|; the bound is 48 u: 0.19 (BF16) and 2.3e-2 (FP16).  Measured: 31 u
-(BF16) and 27 u (FP16).  BF16x3 must meet the FP32 contract (1e-5).
+(BF16) and 27 u (FP16).  BF16x3 must meet the FP32 contract (1e-5), and so
+must the compensated FP32 mode (CUDA cores, Dot2 sums), which is no less
+accurate than the native one.
 """
 import numpy as np
 import pytest
@@ -25,7 +27,7 @@ from conftest import record_error
 pytestmark = pytest.mark.gpu
 
 BOUND = {lgfm.LGF_INTERP_BF16: 48 * 2.0 ** -8, lgfm.LGF_INTERP_FP16: 48 * 2.0 ** -11,
-         lgfm.LGF_INTERP_BF16X3: 1e-5}
+         lgfm.LGF_INTERP_BF16X3: 1e-5, lgfm.LGF_INTERP_COMPENSATED: 1e-5}
 
 
 @pytest.fixture(scope="session", autouse=True)
@@ -62,7 +64,8 @@ def _solve(p, mode, **opts):
 
 
 @pytest.mark.parametrize("n_b", [8, 16])
-@pytest.mark.parametrize("mode", [lgfm.LGF_INTERP_BF16, lgfm.LGF_INTERP_FP16, lgfm.LGF_INTERP_BF16X3])
+@pytest.mark.parametrize("mode", [lgfm.LGF_INTERP_BF16, lgfm.LGF_INTERP_FP16, lgfm.LGF_INTERP_BF16X3,
+                                  lgfm.LGF_INTERP_COMPENSATED])
 def test_mode_against_oracle(n_b, mode):
     p = _problem(n_b)
     ref = _oracle(p)
@@ -71,7 +74,11 @@ def test_mode_against_oracle(n_b, mode):
     record_error(f"{p.name}_nb{n_b}_interp{mode}", fp32_vs_oracle=err, native_fp32_vs_oracle=native)
     print(f"n_b {n_b} mode {mode}: {err:.3e} (native {native:.3e})")
     assert err <= BOUND[mode], (mode, err)
-    assert err >= 0.5 * native or mode == lgfm.LGF_INTERP_BF16X3
+    # (the compensated mode's total error need not be below the native one's
+    # here: the FP32 transforms and products dominate in these shallow trees,
+    # and their rounding pattern decides the maximum; the 5-level 512^3 test
+    # shows the gain where the interpolation sums matter)
+    assert err >= 0.5 * native or mode in (lgfm.LGF_INTERP_BF16X3, lgfm.LGF_INTERP_COMPENSATED)
 
 
 def test_bf16x3_close_to_native_and_split_schedule():
