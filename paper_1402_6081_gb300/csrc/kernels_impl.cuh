@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
                                                      cx<T>* __restrict__ spec) {
     constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NIN | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
     T* X = reinterpret_cast<T*>(B + NIN * PP);
     const R2CItem it = items[blockIdx.x];
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
                                                      int64_t add_stride) {
     constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NOUT | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
     T* O = reinterpret_cast<T*>(B + NOUT * PP);
     const C2RItem it = items[blockIdx.x];
@@ -364,7 +364,59 @@ __device__ __forceinline__ void mirror_rows(cx<T>* sk, int tid, int nthreads) {
     }
 }
 
+// Packed form of the 8 x 8 sibling products (fma.rn.f32x2: two FP32 FMAs per
+// instruction).  With F = Fx + i Fy and K = Kx + i Ky, A accumulates
+// (Fx Kx, Fx Ky) and B accumulates (Fy Kx, Fy Ky), both against K as stored;
+// the complex sum is (A.x - B.y) + i (A.y + B.x).  Half the FMA instructions
+// of persist_block for the same coefficient loads.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void ffma2(uint64_t& d, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ cx<float> unpack_sum(uint64_t A, uint64_t B) {
+    float ax, ay, bx, by;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(ax), "=f"(ay) : "l"(A));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(bx), "=f"(by) : "l"(B));
+    return {ax - by, ay + bx};
+}
+// The 27 coefficients of one source group come as three x-planes of 9 (dy,
+// dz) values: plane dx holds rows centre + dx + 7 dy + 49 dz.  A source group
+// that is the +x neighbour (centre row + 2) of the previous pair's shares its
+// -x plane with that pair's +x plane.  The pair loop keeps three plane
+// register sets whose roles rotate between its two unrolled halves, so the
+// shared plane is reused in place: adjacency only skips its 9 loads.
+__device__ __forceinline__ void persist_plane(uint64_t (&P)[9], const cx<float>* kb) {
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+            P[(dy + 1) + 3 * (dz + 1)] = *reinterpret_cast<const uint64_t*>(kb + (7 * dy + 49 * dz) * 32);
+}
+// the 8 x 8 sibling products of one source group from its -x, centre and +x
+// coefficient planes L, M, R
+__device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
+                                                     const uint64_t (&L)[9], const uint64_t (&M)[9],
+                                                     const uint64_t (&R)[9]) {
+#pragma unroll
+    for (int cs = 0; cs < 8; ++cs) {
+        const uint64_t fx = pk2(F[cs].x, F[cs].x), fy = pk2(F[cs].y, F[cs].y);
+#pragma unroll
+        for (int ct = 0; ct < 8; ++ct) {
+            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
+            const int i = (dy + 1) + 3 * (dz + 1);
+            const uint64_t k = dx < 0 ? L[i] : dx == 0 ? M[i] : R[i];
+            ffma2(A[ct], fx, k);
+            ffma2(B[ct], fy, k);
+        }
+    }
+}
+
 constexpr int kMacWarps = 12;
+constexpr int kMacPackedWarps = 8;   // packed form: 128 registers for two CTAs per SM
 
 // One warp's walk over the (group, neighbour) pairs it owns: groups
 // g0 + warp, g0 + warp + kMacWarps, ... below g1, and for each group the
@@ -387,6 +439,7 @@ __device__ __forceinline__ unsigned nbr_mask(const int* __restrict__ gnbr, int g
 }
 
 // advance to the next pair; returns false past the warp's last group
+template <int WARPS = kMacWarps>
 __device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gnbr, const int* __restrict__ order,
                                          int g1) {
     if (it.mask) {
@@ -394,7 +447,7 @@ __device__ __forceinline__ bool mac_next(MacWalk& it, const int* __restrict__ gn
         it.mask &= it.mask - 1;
         return true;
     }
-    it.g += kMacWarps;
+    it.g += WARPS;
     if (it.g >= g1) return false;
     it.gid = __ldg(order + it.g);
     it.mask = nbr_mask(gnbr, it.gid, it.self);
@@ -440,6 +493,19 @@ __device__ __forceinline__ void mac_block(cx<T> (&acc)[8], const cx<T> (&F)[8], 
         }
 }
 
+// Packed form of mac_block (FP32): the three coefficient planes of the
+// neighbour's centre and the packed 8 x 8 products (persist_block_packed).
+__device__ __forceinline__ void mac_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
+                                                 const cx<float>* __restrict__ sk, int e) {
+    const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
+    const cx<float>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 32 + threadIdx.x;
+    uint64_t L[9], M[9], R[9];
+    persist_plane(L, kb - 32);
+    persist_plane(M, kb);
+    persist_plane(R, kb + 32);
+    persist_block_packed(A, B, F, L, M, R);
+}
+
 // The 343 coefficient rows of the frequencies w0 .. w0+31 into shared memory
 // ([343][32], zero past NW) from the stored half table: eight independent
 // loads per thread in flight before their stores, so a CTA keeps enough
@@ -468,8 +534,8 @@ __device__ __forceinline__ void stage_coefficients(cx<T>* __restrict__ sk, const
 // the warps of one CTA carry similar work).  With include_self the group's own
 // sibling block e = 13 is a source too: that is the merged level-0 / level-1
 // form, where the 343 coefficient rows hold the near offsets as well.
-template <typename T, int S>
-__global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_interval(const cx<T>* __restrict__ fh,
+template <typename T, int S, int WARPS = kMacWarps, bool PACKED = false>
+__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? 2 : 1) k_mac_interval(const cx<T>* __restrict__ fh,
                                                                    const cx<T>* __restrict__ kh,
                                                                    cx<T>* __restrict__ uh,
                                                                    const int* __restrict__ gnbr,
@@ -497,50 +563,59 @@ __global__ void __launch_bounds__(32 * kMacWarps, sizeof(T) == 4 ? 2 : 1) k_mac_
             if (tid == 0) atomicExch(err, 1);
             return;
         }
-        mirror_rows(sk, tid, 32 * kMacWarps);
+        mirror_rows(sk, tid, 32 * WARPS);
         __syncthreads();
     } else {
-        stage_coefficients<T, NW, NWS, 32 * kMacWarps>(sk, kh, w0, tid);
+        stage_coefficients<T, NW, NWS, 32 * WARPS>(sk, kh, w0, tid);
         __syncthreads();
     }
     const int g0 = blockIdx.x * groups_per_cta;
     const int g1 = min(n_groups, g0 + groups_per_cta);
     const int64_t w = w0 + threadIdx.x;
     const int64_t wc = w < NW ? w : NW - 1;
-    MacWalk cur{g0 + int(threadIdx.y) - kMacWarps, -1, 0, 0u, include_self};
-    if (!mac_next(cur, gnbr, order, g1)) return;
+    MacWalk cur{g0 + int(threadIdx.y) - WARPS, -1, 0, 0u, include_self};
+    if (!mac_next<WARPS>(cur, gnbr, order, g1)) return;
     cx<T> Fa[8], Fb[8], acc[8];
+    [[maybe_unused]] uint64_t A[8], B[8];   // packed form (FP32)
+    auto zero = [&] {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
+        for (int c = 0; c < 8; ++c) {
+            acc[c] = czero<T>();
+            if constexpr (PACKED) A[c] = B[c] = 0ull;
+        }
+    };
+    auto block = [&](const cx<T> (&F)[8], int e) {
+        if constexpr (PACKED) mac_block_packed(A, B, F, sk, e);
+        else mac_block(acc, F, sk, e);
+    };
+    // the group's sums out, accumulators cleared
+    auto flush = [&](int gid) {
+        if constexpr (PACKED) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = unpack_sum(A[c], B[c]);
+        }
+        if (w < NW) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) uh[(int64_t(gid) * 8 + c) * NWS + w] = acc[c];
+        }
+        zero();
+    };
+    zero();
     mac_load<T, S>(Fa, fh, gnbr, cur, wc);
     // two pairs per trip so the prefetch buffers alternate without copies
     while (true) {
         MacWalk nxt = cur;
-        bool more = mac_next(nxt, gnbr, order, g1);
+        bool more = mac_next<WARPS>(nxt, gnbr, order, g1);
         if (more) mac_load<T, S>(Fb, fh, gnbr, nxt, wc);
-        if (cur.e >= 0) mac_block(acc, Fa, sk, cur.e);
-        if (!more || nxt.g != cur.g) {
-            if (w < NW) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.gid) * 8 + c) * NWS + w] = acc[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
-        }
+        if (cur.e >= 0) block(Fa, cur.e);
+        if (!more || nxt.g != cur.g) flush(cur.gid);
         if (!more) break;
         cur = nxt;
         nxt = cur;
-        more = mac_next(nxt, gnbr, order, g1);
+        more = mac_next<WARPS>(nxt, gnbr, order, g1);
         if (more) mac_load<T, S>(Fa, fh, gnbr, nxt, wc);
-        if (cur.e >= 0) mac_block(acc, Fb, sk, cur.e);
-        if (!more || nxt.g != cur.g) {
-            if (w < NW) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) uh[(int64_t(cur.gid) * 8 + c) * NWS + w] = acc[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
-        }
+        if (cur.e >= 0) block(Fb, cur.e);
+        if (!more || nxt.g != cur.g) flush(cur.gid);
         if (!more) break;
         cur = nxt;
     }
@@ -733,7 +808,7 @@ __global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T
                                                                      int groups_per_cta) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][64]
     const int64_t w0 = int64_t(blockIdx.y) * 64;
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -831,7 +906,7 @@ __global__ void __launch_bounds__(32 * kMacPWarps, 1) k_mac_interval_pair(const 
                                                                          int include_self) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][32]
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -934,57 +1009,6 @@ __device__ __forceinline__ void persist_block(cx<float> (&acc)[8], const cx<floa
         }
 }
 
-// Packed form of the 8 x 8 sibling products (fma.rn.f32x2: two FP32 FMAs per
-// instruction).  With F = Fx + i Fy and K = Kx + i Ky, A accumulates
-// (Fx Kx, Fx Ky) and B accumulates (Fy Kx, Fy Ky), both against K as stored;
-// the complex sum is (A.x - B.y) + i (A.y + B.x).  Half the FMA instructions
-// of persist_block for the same coefficient loads.
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void ffma2(uint64_t& d, uint64_t a, uint64_t b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ cx<float> unpack_sum(uint64_t A, uint64_t B) {
-    float ax, ay, bx, by;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(ax), "=f"(ay) : "l"(A));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(bx), "=f"(by) : "l"(B));
-    return {ax - by, ay + bx};
-}
-// The 27 coefficients of one source group come as three x-planes of 9 (dy,
-// dz) values: plane dx holds rows centre + dx + 7 dy + 49 dz.  A source group
-// that is the +x neighbour (centre row + 2) of the previous pair's shares its
-// -x plane with that pair's +x plane.  The pair loop keeps three plane
-// register sets whose roles rotate between its two unrolled halves, so the
-// shared plane is reused in place: adjacency only skips its 9 loads.
-__device__ __forceinline__ void persist_plane(uint64_t (&P)[9], const cx<float>* kb) {
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-            P[(dy + 1) + 3 * (dz + 1)] = *reinterpret_cast<const uint64_t*>(kb + (7 * dy + 49 * dz) * 32);
-}
-// the 8 x 8 sibling products of one source group from its -x, centre and +x
-// coefficient planes L, M, R
-__device__ __forceinline__ void persist_block_packed(uint64_t (&A)[8], uint64_t (&B)[8], const cx<float> (&F)[8],
-                                                     const uint64_t (&L)[9], const uint64_t (&M)[9],
-                                                     const uint64_t (&R)[9]) {
-#pragma unroll
-    for (int cs = 0; cs < 8; ++cs) {
-        const uint64_t fx = pk2(F[cs].x, F[cs].x), fy = pk2(F[cs].y, F[cs].y);
-#pragma unroll
-        for (int ct = 0; ct < 8; ++ct) {
-            const int dx = (cs & 1) - (ct & 1), dy = ((cs >> 1) & 1) - ((ct >> 1) & 1), dz = (cs >> 2) - (ct >> 2);
-            const int i = (dy + 1) + 3 * (dz + 1);
-            const uint64_t k = dx < 0 ? L[i] : dx == 0 ? M[i] : R[i];
-            ffma2(A[ct], fx, k);
-            ffma2(B[ct], fy, k);
-        }
-    }
-}
-
 // Store of a product spectrum value with an L2 evict-last policy: the level-0
 // inverse FFT reads these spectra right after the launch, and the launch's own
 // traffic (source spectra, coefficient chunks) would otherwise push them out.
@@ -1010,7 +1034,7 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                   const __grid_constant__ CUtensorMap tmap, int use_tma) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);                 // [2][343][32]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * kPersistBuf);   // [2] copy landed
     uint64_t* ready = full + 2;                                                // [2] rows mirrored
@@ -1265,7 +1289,7 @@ __global__ void __launch_bounds__(cube_threads<S>(), 1)
     constexpr unsigned PLANE = PP * unsigned(sizeof(cx<float>)), ROWB = NIN * 4u, SWZ = ROWB / 16 - 1;
     static_assert(NIN == H && S % 4 == 0 && (NIN == 16 || NIN == 8) && PP % 2 == 0,
                   "64B or 32B swizzled rows; bulk copies move 16-byte multiples");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<float>* P = reinterpret_cast<cx<float>*>(smem_raw);   // [2][H planes]
     cx<float>* XB = P + S * PP;                               // [NL rows][RP]
     const uintptr_t xa = (reinterpret_cast<uintptr_t>(XB + NL * RP) + 1023) & ~uintptr_t(1023);
@@ -1415,7 +1439,7 @@ __global__ void __launch_bounds__(cube_threads<S>(), 1)
     constexpr int64_t NWS = (int64_t(PP) * S + 31) / 32 * 32;
     constexpr unsigned PLANE = PP * unsigned(sizeof(cx<float>));
     static_assert(NOUT == S / 2 && S % 8 == 0 && PP % 2 == 0, "bulk copies move 16-byte multiples");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     cx<float>* B = reinterpret_cast<cx<float>*>(smem_raw);   // S planes
     cx<float>* YB = B + S * PP;                               // [NL rows (z, y)][RP]
     float* O = reinterpret_cast<float*>(YB + NL * RP);        // [NL rows][RS]
@@ -1851,7 +1875,7 @@ __global__ void __launch_bounds__(kRegThreads) k_reg_wide(const T* __restrict__ 
                                                           const int* __restrict__ parent_slot,
                                                           T* __restrict__ dst, const InterpW<T, NI> W) {
     constexpr int NB = NI - 1, N2 = NI * NI, N3 = NI * NI * NI;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     T* a = reinterpret_cast<T*>(smem_raw);   // [4][NI][NI][NI] = [cx + 2cy][pz][y][x]
     const int t = threadIdx.x;
     // z pass (4 N2 items, a thread may take two)
@@ -2124,14 +2148,20 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
         kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
         return cudaGetLastError();
     }
+    // FP32 outside variant 1: packed two-wide FMAs, 8 warps of up to 128
+    // registers (two CTAs per SM); variant 1 and FP64: one FMA per real
+    // product, 12 warps
+    const bool packed = sizeof(T) == 4 && variant != 1;
+    const int warps = packed ? dev::kMacPackedWarps : dev::kMacWarps;
     const size_t smem = sizeof(dev::cx<T>) * 343 * 32 + 16;
-    auto kern = dev::k_mac_interval<T, S>;
+    auto kern = packed ? dev::k_mac_interval<T, S, dev::kMacPackedWarps, sizeof(T) == 4>
+                       : dev::k_mac_interval<T, S, dev::kMacWarps, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (n_groups == 0) return cudaSuccess;
     const int64_t nchunks = (NW + 31) / 32;
-    const int per = groups_per_cta(dev::kMacWarps, sizeof(T) == 4 ? 2 : 1, nchunks);
-    dim3 block(32, dev::kMacWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
+    const int per = groups_per_cta(warps, sizeof(T) == 4 ? 2 : 1, nchunks);
+    dim3 block(32, warps), grid((n_groups + per - 1) / per, unsigned(nchunks));
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (tmap) map = *tmap;
