@@ -1040,9 +1040,16 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
     uint64_t* ready = full + 2;                                                // [2] rows mirrored
     int* ctr = reinterpret_cast<int*>(ready + 2);                            // [2] next position
     int* done = ctr + 2;                                                     // [2] warps finished
-    const long long u0 = cta_units[blockIdx.x], u1 = cta_units[blockIdx.x + 1];
-    if (u0 >= u1) return;
-    const long long c0 = u0 / n_groups, c1 = (u1 - 1) / n_groups;
+    // this CTA's work: whole chunks [m0, m1), then the units [r0, r1) of the
+    // chunks left over (unit = chunk * n_groups + position); visit j is the
+    // j-th chunk of that sequence with its positions [pb, pe)
+    const long long* cu = cta_units + 4 * int64_t(blockIdx.x);
+    const long long m0 = cu[0], m1 = cu[1], r0 = cu[2], r1 = cu[3];
+    const int nm = int(m1 - m0);
+    const long long rc0 = r1 > r0 ? r0 / n_groups : 0, rc1 = r1 > r0 ? (r1 - 1) / n_groups : -1;
+    const int V = nm + int(rc1 - rc0 + 1);
+    if (V <= 0) return;
+    auto chunk_of = [&](int j) -> long long { return j < nm ? m0 + j : rc0 + (j - nm); };
     const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
     const uint64_t keep = l2_evict_last_policy();
     if (threadIdx.x == 0) {
@@ -1055,11 +1062,12 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // one warp loads chunk c: the stored rows by one tensor box (or 172 row
-    // copies), then, once they landed, the mirrored rows by conjugation;
-    // ready[b] releases the chunk to every warp
-    auto issue = [&](long long c) {
-        const int b = int((c - c0) & 1);
+    // one warp loads visit j's chunk: the stored rows by one tensor box (or
+    // 172 row copies), then, once they landed, the mirrored rows by
+    // conjugation; ready[b] releases the chunk to every warp
+    auto issue = [&](int j) {
+        const int b = j & 1;
+        const long long c = chunk_of(j);
         cx<float>* dst = buf + b * (343 * 32) + kSymFirst * 32;
         if (use_tma) {
             if (lane == 0) {
@@ -1073,9 +1081,9 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
         const cx<float>* src = kh + c * 32;
         for (int r = lane; r < kSymRows; r += 32) bulk_g2s(dst + r * 32, src + int64_t(r) * NWS, 256u, &full[b]);
     };
-    auto finish = [&](long long c) {
-        const int b = int((c - c0) & 1);
-        if (mbar_wait(&full[b], unsigned(((c - c0) >> 1) & 1))) {
+    auto finish = [&](int j) {
+        const int b = j & 1;
+        if (mbar_wait(&full[b], unsigned((j >> 1) & 1))) {
             cx<float>* t = buf + b * (343 * 32);
             for (int r = 0; r < kSymFirst; ++r) t[r * 32 + lane] = conjx(t[(2 * kSymFirst - r) * 32 + lane]);
         } else if (lane == 0) {
@@ -1085,20 +1093,21 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[b])) : "memory");
     };
     if (warp == 0) {
-        issue(c0);
-        if (c1 > c0) issue(c0 + 1);
-        finish(c0);
-        if (c1 > c0) finish(c0 + 1);
+        issue(0);
+        if (V > 1) issue(1);
+        finish(0);
+        if (V > 1) finish(1);
     }
-    for (long long c = c0; c <= c1; ++c) {
-        const int b = int((c - c0) & 1);
-        if (!mbar_wait(&ready[b], unsigned(((c - c0) >> 1) & 1))) {
+    for (int j = 0; j < V; ++j) {
+        const int b = j & 1;
+        if (!mbar_wait(&ready[b], unsigned((j >> 1) & 1))) {
             if (lane == 0) atomicExch(err, 1);
             return;
         }
+        const long long c = chunk_of(j);
         const cx<float>* sk = buf + b * (343 * 32) + lane;
-        const int pb = c == c0 ? int(u0 % n_groups) : 0;
-        const int pe = c == c1 ? int((u1 - 1) % n_groups) + 1 : n_groups;
+        const int pb = j >= nm && c == rc0 ? int(r0 % n_groups) : 0;
+        const int pe = j >= nm && c == rc1 ? int((r1 - 1) % n_groups) + 1 : n_groups;
         const int64_t w = c * 32 + lane;
         const int64_t wc = w < NW ? w : NW - 1;
         while (true) {
@@ -1168,8 +1177,8 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 for (int i = 0; i < 8; ++i) st_keep(out + i * NWS, acc[i], keep);
             }
         }
-        // this warp is done with chunk c; the last one out refills the buffer
-        // with chunk c + 2 (every read of the buffer has completed by then)
+        // this warp is done with visit j; the last one out refills the buffer
+        // with visit j + 2 (every read of the buffer has completed by then)
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -1181,10 +1190,10 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
                 ctr[b] = 0;
                 done[b] = 0;
             }
-            if (c + 2 <= c1) {
+            if (j + 2 < V) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(c + 2);
-                finish(c + 2);
+                issue(j + 2);
+                finish(j + 2);
             }
         }
     }

@@ -88,16 +88,18 @@ struct C2RItem { int src; int dst; int aux; };
 
 // Work lists of the persistent interaction kernel: per group, in work order,
 // its source groups with the coefficient row of their centre offset d = 2e
-// (row (dx+3) + 7 (dy+3) + 49 (dz+3) of the 7^3 table); the launch's units
-// (frequency chunk * n_groups + position) split into n_cta ranges of about
-// equal work; err is set when a wait in the kernel runs out.
+// (row (dx+3) + 7 (dy+3) + 49 (dz+3) of the 7^3 table).  Each CTA takes
+// floor(chunks / n_cta) whole frequency chunks and then a range of about
+// equal work of the units (chunk * n_groups + position) of the chunks left
+// over, so it stages as few chunks as it can; err is set when a wait in the
+// kernel runs out.
 struct PairSrc { int src; int centre; };
 struct PersistPlan {
     const CUtensorMap* tmap = nullptr;   // the level's kernel table as a 2D tensor (rows x 2 NWS reals)
     const PairSrc* pairs = nullptr;
     const int* start = nullptr;          // n_groups + 1 offsets into pairs
     const int* order = nullptr;          // group id per position
-    const long long* cta_units = nullptr;    // n_cta + 1
+    const long long* cta_units = nullptr;    // n_cta x {m0, m1, r0, r1}: whole chunks, then leftover units
     int n_groups = 0, n_cta = 0;
     int* err = nullptr;
     bool packed = false;                 // fma.rn.f32x2 form of the products

@@ -561,24 +561,34 @@ static lgf_status build_persist(lgf_plan_s* P, DevLevel& D, const std::vector<in
     std::vector<long long> pre(size_t(G) + 1, 0);
     for (int pos = 0; pos < G; ++pos)
         pre[size_t(pos) + 1] = pre[size_t(pos)] + (start[size_t(pos) + 1] - start[size_t(pos)]) + 1;
-    const long long Wg = pre[size_t(G)], Wt = Wg * chunks;
+    // every CTA first takes q whole chunks (a chunk staged for only part of
+    // its groups costs as much as a whole one), then about equal work of the
+    // units of the chunks left over
+    const long long Wg = pre[size_t(G)], q = chunks / n_cta, rc = q * n_cta, Wr = Wg * (chunks - rc);
     std::vector<long long> cut(size_t(n_cta) + 1);
     for (long long b = 0; b <= n_cta; ++b) {
-        const long long T = (Wt * b) / n_cta;
-        const long long c = std::min(T / Wg, chunks);
+        const long long T = (Wr * b) / n_cta;
+        const long long c = std::min(T / Wg, chunks - rc);
         const long long pos = std::lower_bound(pre.begin(), pre.end(), T - c * Wg) - pre.begin();
-        cut[size_t(b)] = std::min(c * G + std::min<long long>(pos, G), chunks * G);
+        cut[size_t(b)] = std::min((rc + c) * G + std::min<long long>(pos, G), chunks * G);
     }
-    cut[0] = 0;
+    cut[0] = rc * G;
     cut[size_t(n_cta)] = chunks * G;
     for (size_t b = 1; b < cut.size(); ++b) cut[b] = std::max(cut[b], cut[b - 1]);
+    std::vector<long long> units(size_t(4 * n_cta));
+    for (long long b = 0; b < n_cta; ++b) {
+        units[size_t(4 * b)] = q * b;
+        units[size_t(4 * b + 1)] = q * (b + 1);
+        units[size_t(4 * b + 2)] = cut[size_t(b)];
+        units[size_t(4 * b + 3)] = cut[size_t(b) + 1];
+    }
     lgf_status s;
     PairSrc* dp = nullptr;
     int* ds = nullptr;
     long long* dc = nullptr;
     if ((s = upload(P, pairs, &dp)) != LGF_OK) return s;
     if ((s = upload(P, start, &ds)) != LGF_OK) return s;
-    if ((s = upload(P, cut, &dc)) != LGF_OK) return s;
+    if ((s = upload(P, units, &dc)) != LGF_OK) return s;
     D.pp.pairs = dp;
     D.pp.start = ds;
     D.pp.order = D.order;
