@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
     const R2CItem it = items[blockIdx.x];
     const T* in = src + int64_t(it.src) * src_stride;
     cx<T>* out = spec + int64_t(it.dst) * NWS;
+    // a kernel launched after this one with programmatic serialization (the
+    // level-0 products) may start its prologue once every CTA got here; it
+    // waits for this grid to finish before it reads the spectra
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     staged_copy<T>(NIN * NIN * NIN, in, [&](int i, T v) { X[(i / NIN) * RS + i % NIN] = v; });
     __syncthreads();
@@ -1098,6 +1102,10 @@ __global__ void __launch_bounds__(32 * WARPS, 1)
         finish(0);
         if (V > 1) finish(1);
     }
+    // launched early behind the forward FFT (programmatic serialization): the
+    // coefficient staging above needs only the kernel tables; the source
+    // spectra are read after the FFT's grid has completed (a no-op otherwise)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int j = 0; j < V; ++j) {
         const int b = j & 1;
         if (!mbar_wait(&ready[b], unsigned((j >> 1) & 1))) {
@@ -2193,8 +2201,11 @@ cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, co
 #undef LGF_MACI
 }
 
+// early: programmatic serialization behind the kernel just launched on st
+// (the level-0 forward FFT), so the CTAs stage their first coefficient chunks
+// while that grid drains
 template <int S, int WARPS, bool PACKED>
-static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp,
+static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int early,
                                       cudaStream_t st) {
     auto kern = dev::k_mac_persist<S, WARPS, PACKED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::kPersistSmem));
@@ -2203,28 +2214,36 @@ static cudaError_t launch_mac_persist(const void* fh, const void* kh, void* uh, 
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (pp.tmap) map = *pp.tmap;
-    kern<<<pp.n_cta, 32 * WARPS, dev::kPersistSmem, st>>>(
-        static_cast<const dev::cx<float>*>(fh), static_cast<const dev::cx<float>*>(kh),
-        static_cast<dev::cx<float>*>(uh), pp.pairs, pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err, map,
-        pp.tmap ? 1 : 0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(pp.n_cta));
+    cfg.blockDim = dim3(32u * WARPS);
+    cfg.dynamicSmemBytes = dev::kPersistSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const dev::cx<float>*>(fh),
+                              static_cast<const dev::cx<float>*>(kh), static_cast<dev::cx<float>*>(uh), pp.pairs,
+                              pp.start, pp.order, pp.cta_units, pp.n_groups, pp.err, map, pp.tmap ? 1 : 0);
 }
 
 template <int S>
-static cudaError_t launch_mac_persist_form(const void* fh, const void* kh, void* uh, const PersistPlan& pp,
+static cudaError_t launch_mac_persist_form(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int early,
                                            cudaStream_t st) {
-    if (pp.packed) return launch_mac_persist<S, dev::kPersistWarpsPacked, true>(fh, kh, uh, pp, st);
-    return launch_mac_persist<S, dev::kPersistWarps, false>(fh, kh, uh, pp, st);
+    if (pp.packed) return launch_mac_persist<S, dev::kPersistWarpsPacked, true>(fh, kh, uh, pp, early, st);
+    return launch_mac_persist<S, dev::kPersistWarps, false>(fh, kh, uh, pp, early, st);
 }
 
 template <typename T>
 cudaError_t Launch<T>::mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
-                                   cudaStream_t st) {
+                                   int early, cudaStream_t st) {
     if constexpr (sizeof(T) != 4) {
         return cudaErrorInvalidValue;
     } else {
 #define LGF_MACP(SS) \
-    case SS: return launch_mac_persist_form<SS>(fh, kh, uh, pp, st);
+    case SS: return launch_mac_persist_form<SS>(fh, kh, uh, pp, early, st);
         switch (S) {
             LGF_MACP(8) LGF_MACP(10) LGF_MACP(16) LGF_MACP(17) LGF_MACP(18) LGF_MACP(32) LGF_MACP(33) LGF_MACP(34)
             LGF_MACP(36)

@@ -129,8 +129,10 @@ struct Launch {
                                     int* err, cudaStream_t st);
     // The same products as mac_interval from a persistent kernel (one CTA per
     // SM) that stages the coefficient chunks with bulk copies; FP32 only.
+    // early: launched with programmatic serialization behind the forward FFT
+    // that precedes it on st (the FFT kernel signals its dependents).
     static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
-                                   cudaStream_t st);
+                                   int early, cudaStream_t st);
     // Reg of 8 children into each parent: items (parent slot, child group, child-src kind).
     // comp (FP32): compensated sums (interpolation mode COMPENSATED).
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block,

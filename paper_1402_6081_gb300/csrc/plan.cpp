@@ -1048,7 +1048,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             DevLevel& D = lev[size_t(l)];
             if (!D.m2l) continue;
             e = timed(P, "mac_interval_l2plus", s2, [&] {
-                if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s2);
+                if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s2);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
                                         0, table_map(D), P->err, s2);
             });
@@ -1096,7 +1096,11 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     if (split) LGF_CUDA(wait(st, 1));
     if (P->merged) {
         e = timed(P, "mac_level01", st, [&] {
-            if (uses_persist(P, 0)) return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, st);
+            // directly behind the forward FFT on st (no event between them):
+            // launched early, it stages its first coefficient chunks meanwhile
+            const int early = !split && P->ev.empty() ? 1 : 0;
+            if (uses_persist(P, 0))
+                return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, early, st);
             return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
                                     P->S0, P->interval_kernel == 3 ? 3 : 1, 1, table_map(lev[0]), P->err, st);
         });
@@ -1133,7 +1137,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
             if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
             e = timed(P, "mac_interval_l1", s1, [&] {
-                if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, s1);
+                if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s1);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
                                         0, table_map(D), P->err, s1);
             });
