@@ -123,13 +123,16 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      unrolled 4^3-source form, 2 = half-plane pipelined form
  *   interval_kernel    product kernel of levels >= 1 (and of the merged
  *                      level-0/1 pass): 0 = default (5 for FP32 plans where a
- *                      level has >= 48 sibling groups, else 1), 1 = one
- *                      frequency per thread, one CTA per
- *                      (frequency chunk, group range), 2 = two frequencies per
+ *                      level has >= 48 sibling groups; elsewhere one CTA per
+ *                      (frequency chunk, group range) with the packed FP32
+ *                      products of form 5, 8 warps), 1 = one frequency per
+ *                      thread, one CTA per (frequency chunk, group range), one
+ *                      FMA per real product, 2 = two frequencies per
  *                      thread, 3 = two sibling groups per warp sharing
- *                      coefficient loads, 4 = persistent: one CTA per SM over
- *                      a plan-time range of equal work, coefficient chunks
- *                      staged by bulk copies into two shared-memory buffers
+ *                      coefficient loads, 4 = persistent: one CTA per SM,
+ *                      each taking whole frequency chunks and then an equal
+ *                      share of the chunks left over, coefficient chunks
+ *                      staged by tensor copies into two shared-memory buffers,
  *                      5 = form 4 with the products as packed two-wide FP32
  *                      FMAs (fma.rn.f32x2), 16 warps per CTA
  *                      (2, 3, 4 and 5: FP32 only; FP64 plans use 1).  A wait

@@ -723,14 +723,17 @@ __device__ __forceinline__ cx2<T> ld2(const cx<T>* p) {
 template <typename T>
 __device__ __forceinline__ cx2<T> lds2(const cx<T>* p) {
     cx2<T> r;
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        r.a = {v.x, v.y};
-        r.b = {v.z, v.w};
-    } else {
-        r.a = p[0];
-        r.b = p[1];
-    }
+    r.a = p[0];
+    r.b = p[1];
+    return r;
+}
+// FP32: both values in one 16-byte load
+template <>
+__device__ __forceinline__ cx2<float> lds2<float>(const cx<float>* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    cx2<float> r;
+    r.a = {v.x, v.y};
+    r.b = {v.z, v.w};
     return r;
 }
 
