@@ -208,7 +208,7 @@ def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra |
 
     # Step 1, upward pass: sources at nodes, then padded forward FFTs.
     ft = {}                                    # f~ per level: dict interval -> n_I^3
-    fh = {0: {P: np.fft.rfftn(f[bidx[P]], s=(S0, S0, S0)) for P in levels[0]}}
+    fh = {0: {P: np.fft.rfftn(f[bidx[P]], s=(S0, S0, S0), axes=(0, 1, 2)) for P in levels[0]}}
     for l in range(1, L + 1):
         ft[l] = {}
         for P in levels[l]:
@@ -222,7 +222,7 @@ def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra |
                     if Q in ft[l - 1]:
                         x += reg(W, _child_pos(Q), ft[l - 1][Q])
             ft[l][P] = x
-        fh[l] = {P: np.fft.rfftn(ft[l][P], s=(S, S, S)) for P in levels[l]}
+        fh[l] = {P: np.fft.rfftn(ft[l][P], s=(S, S, S), axes=(0, 1, 2)) for P in levels[l]}
 
     # Step 2, level interactions: sum of spectral products over InflList.
     uh = {}
@@ -243,13 +243,13 @@ def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra |
         ut[l] = {}
         for P in levels[l]:
             v = (np.zeros((n_I, n_I, n_I)) if uh[l][P] is None
-                 else np.fft.irfftn(uh[l][P], s=(S, S, S))[:n_I, :n_I, :n_I])
+                 else np.fft.irfftn(uh[l][P], s=(S, S, S), axes=(0, 1, 2))[:n_I, :n_I, :n_I])
             if l < L:
                 v = v + interp(W, _child_pos(P), ut[l + 1][_parent(P)])
             ut[l][P] = v
     u = np.empty_like(f)
     for P in levels[0]:
-        v = np.fft.irfftn(uh[0][P], s=(S0, S0, S0))[:n_b, :n_b, :n_b]
+        v = np.fft.irfftn(uh[0][P], s=(S0, S0, S0), axes=(0, 1, 2))[:n_b, :n_b, :n_b]
         u[bidx[P]] = v + ut[1][P][:n_b, :n_b, :n_b]
     return u
 

@@ -50,7 +50,7 @@ def test_block_fft_convolution_matches_dense_sum():
     fq = rng.standard_normal((n_b, n_b, n_b))              # [z, y, x]
     S = 2 * n_b
     k = fmm.kernel_vector(h, d, n_b, n_b, S)
-    u = np.fft.irfftn(np.fft.rfftn(fq, s=(S, S, S)) * np.fft.rfftn(k), s=(S, S, S))[:n_b, :n_b, :n_b]
+    u = np.fft.irfftn(np.fft.rfftn(fq, s=(S, S, S), axes=(0, 1, 2)) * np.fft.rfftn(k), s=(S, S, S), axes=(0, 1, 2))[:n_b, :n_b, :n_b]
     ref = np.zeros_like(u)
     for iz, iy, ix in np.ndindex(n_b, n_b, n_b):
         s = 0.0
