@@ -1292,16 +1292,17 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     }
     if (P->free_sms == 0) {
         // Default schedule of the persistent products: when levels >= 2 carry
-        // a tenth or more of the level-0/1 pair work they get every SM after
-        // the products (split); below that they run beside them on 24 SMs.
-        // Measured on GB300: 128^3 torus (ratio 0.05) 0.275 ms with 24 SMs vs
-        // 0.315 split; 512^3 full box (0.11) 21.8 ms split vs 22.3.
+        // 7% or more of the level-0/1 pair work they get every SM after the
+        // products (split); below that they run beside them on 24 SMs.
+        // Measured on GB300 (ms, split / 24 SMs): 128^3 torus (ratio 0.05)
+        // 0.280 / 0.252; 256^3 box (0.09) 2.254 / 2.307; 512^3 box (0.11)
+        // 19.82 / 20.43; 512^3 irregular (0.12) 5.48 / 5.85.
         double main = 0, side = 0;
         for (const HostPlan& H : hp) {
             main += double(H.pairs[0] + (H.L >= 1 ? H.pairs[1] : 0)) * double(nw_of(P->S0));
             for (int l = 2; l <= H.L; ++l) side += double(H.pairs[size_t(l)]) * double(nw_of(P->SI));
         }
-        P->free_sms = side > 0.1 * main ? -1 : 24;
+        P->free_sms = side > 0.07 * main ? -1 : 24;
     }
     s = build_plan(P.get(), hp);
     if (s != LGF_OK) return s;
