@@ -411,9 +411,12 @@ def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
         s["rejected"] = len(rejected)
         s["plans_resident"] = sum(len(v) for v in srv.pools.slots.values())
         s["hbm_used_gb"] = srv.pools.used / 1e9
-        # the same 512^3 request alone
-        alone, _ = srv.run([Request(0, 0.0, big, problems[big].n_points)])
-        s["big_512_alone_ms"] = 1e3 * alone[0].latency
+        # the same 512^3 request alone: the first run right after the stream
+        # carries a one-time transient (56.8 ms against 25.2 ms in a probe), so
+        # it is kept apart and the median of the three runs after it reported
+        alone = [srv.run([Request(0, 0.0, big, problems[big].n_points)])[0][0].latency for _ in range(4)]
+        s["big_512_alone_first_ms"] = 1e3 * alone[0]
+        s["big_512_alone_ms"] = 1e3 * float(np.median(alone[1:]))
         # saturated: every timed request present at once (capacity); the
         # second pass, once the pools hold the plans this load needs
         sat = [Request(r.rid, 0.0, r.key, r.n_points) for r in reqs if n_warm <= r.rid < n_requests]
