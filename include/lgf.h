@@ -48,7 +48,7 @@ typedef struct lgf_plan_s *lgf_plan;
 typedef enum {
     LGF_OK = 0,
     LGF_ERR_INVALID_ARG = 1,   /* bad pointer, size, duplicate block, ...     */
-    LGF_ERR_UNSUPPORTED = 2,   /* valid request this build does not handle     */
+    LGF_ERR_UNSUPPORTED = 2,   /* valid request the library does not handle    */
     LGF_ERR_OOM = 3,           /* device or host allocation failed            */
     LGF_ERR_CUDA = 4,          /* CUDA runtime error (message has details)     */
     LGF_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
