@@ -330,7 +330,14 @@ def lgf_interp_weights(n_b: int, n_max: int) -> np.ndarray:
 
 class Solver:
     """Owns one plan: ``Solver(blocks, n_b, n_levels, order, precision)(f) -> u``
-    with f, u torch CUDA tensors of shape (n_blocks, n_b, n_b, n_b)."""
+    with f, u torch CUDA tensors of shape (n_blocks, n_b, n_b, n_b).
+
+    The keyword options are those of ``lgf_plan_options`` in include/lgf.h
+    (0 = the library's choice): the interval FFT length, the product-kernel
+    forms, the stream use, the separate level-1 form, the SMs left beside the
+    persistent products, and the level-0 FFT form.  ``interp_mode`` selects the
+    Reg/Interp arithmetic of FP32 plans (native, BF16/FP16/BF16x3 on the
+    tensor cores, or compensated FP32 sums)."""
 
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
