@@ -106,6 +106,40 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def measure_fma_peaks(lgfm, dev: int):
+    """FP32 and FP64 fused multiply-add throughput of this GPU, measured by the
+    library (lgf_measure_fma_peak: every SM, independent FMA chains, best of 5
+    launches), with the SM clock sampled meanwhile.  TFLOP/s."""
+    clk = ClockSampler(dev)
+    clk.start()
+    r = {name: lgfm.lgf_measure_fma_peak(kind, 5) for name, kind in (("fp64", 0), ("fp32", 1), ("fp32x2", 2))}
+    c = clk.stop()
+    out = {k: {"tflops": v[0] / 1e12, "ms": v[1]} for k, v in r.items()}
+    out["fp32_best_tflops"] = max(out["fp32"]["tflops"], out["fp32x2"]["tflops"])
+    out["clocks"] = c
+    out["how"] = ("lgf_measure_fma_peak: every SM full of 256-thread CTAs, 16 independent fma.rn chains per "
+                  "thread (f64 / f32 / f32x2), CUDA events, best of 5; 2 flop per FMA lane")
+    return out
+
+
 def profiled_traffic(name: str):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
     summary (profiles/<kernel>_torus_box_128_fp32.md), or None when there is
@@ -196,7 +230,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": "window64", "points": p.n_points},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "nproc": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -294,7 +328,9 @@ def irregular_run(torch, lgfm, steps: int, flush):
     the FP64 oracle at 1e-12 on the other configs)."""
     p = W.tori_irregular(2)
     stream = torch.cuda.Stream()
-    modes = {"fp32": lgfm.LGF_INTERP_NATIVE, "fp32_compensated": lgfm.LGF_INTERP_COMPENSATED,
+    # "fp32": the library's default (compensated Reg/Interp sums at this depth);
+    # "fp32_plain": plain FP32 sums
+    modes = {"fp32": lgfm.LGF_INTERP_NATIVE, "fp32_plain": lgfm.LGF_INTERP_PLAIN,
              "bf16": lgfm.LGF_INTERP_BF16, "fp16": lgfm.LGF_INTERP_FP16, "bf16x3": lgfm.LGF_INTERP_BF16X3}
 
     def run(prec, mode, k):
@@ -334,7 +370,7 @@ def irregular_run(torch, lgfm, steps: int, flush):
     return out
 
 
-def fft_conv_run(torch, lgfm, steps: int, flush):
+def fft_conv_run(torch, lgfm, steps: int, flush, peak_tf: float):
     """The FFT-convolution special case (Sec. 4, "FFT Conv."): every 16^3 block
     an isolated one-block domain, u_b = G * f_b by one padded 32^3 R2C, one
     spectral product and one truncated C2R (lgf_solve_blocks_noalloc, 232
@@ -372,10 +408,10 @@ def fft_conv_run(torch, lgfm, steps: int, flush):
     n3 = S ** 3
     flops_block = 2 * 5.0 * n3 * np.log2(n3) / 2 + 8.0 * (S // 2 + 1) * S * S
     tf = nblk * flops_block / (ms * 1e-3) / 1e12
-    peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     return {"value": p.n_points / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms, "steps": steps,
             "launch_calls_per_step": -(-nblk // per_call),
             "roofline": {"bound": "alu", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
+                         "peak_source": "measured FP32 FMA peak (lgf_measure_fma_peak)",
                          "algorithmic": "per block: 5 N log2 N / 2 per real 32^3 transform x 2 + 8 flop per "
                                         "complex product",
                          "hbm_gbs_f_and_u": 8.0 * p.n_points / (ms * 1e-3) / 1e9},
@@ -557,7 +593,7 @@ def main():
     ms64, _ = timed_steps(s64, f64, u64, k64, 3)
     rate64 = npts / (statistics.mean(ms64) * 1e-3)
 
-    # end to end through the public API with host buffers (pinned), copies inside
+    # end to end through the C ABI with host buffers (pinned), copies inside
     fh = torch.from_numpy(p.f).float().pin_memory()
     uh = torch.empty_like(fh).pin_memory()
     k_e2e = max(3, min(500, args.steps // 4))
@@ -567,44 +603,19 @@ def main():
     for _ in range(k_e2e):
         lgfm.lgf_solve_host(s32.plan, fh, uh, stream)
     e2e_serial_s = (time.perf_counter() - t0) / k_e2e
-    # pipelined: one plan solving in order on its stream; each step's input
-    # copy runs ahead on an H2D stream and its result copy behind on a D2H
-    # stream, into and out of double-buffered device arrays, so the copies
-    # of neighbouring steps overlap the solve; every step still copies its
-    # input in and its result out
-    h2d_st, d2h_st = torch.cuda.Stream(), torch.cuda.Stream()
-    fds, uds = [f32, torch.empty_like(f32)], [u32, torch.empty_like(u32)]
+    # pipelined, one C-ABI call for all steps (lgf_solve_host_pipelined): each
+    # step's input copy runs ahead of its solve and its result copy behind it
+    # on library-owned copy streams, through double-buffered device arrays;
+    # every step still copies its input in and its result out
     uhs = [uh, torch.empty_like(uh).pin_memory()]
-    in_ready = [torch.cuda.Event() for _ in range(2)]
-    solved = [torch.cuda.Event() for _ in range(2)]
-    out_done = [torch.cuda.Event() for _ in range(2)]
-
-    def e2e_step(k):
-        b = k % 2
-        with torch.cuda.stream(h2d_st):
-            if k >= 2:
-                h2d_st.wait_event(solved[b])     # the solve of step k-2 has read fds[b]
-            fds[b].copy_(fh, non_blocking=True)
-            in_ready[b].record(h2d_st)
-        stream.wait_event(in_ready[b])
-        if k >= 2:
-            stream.wait_event(out_done[b])       # step k-2's result has left uds[b]
-        s32(fds[b], uds[b], stream)
-        solved[b].record(stream)
-        with torch.cuda.stream(d2h_st):
-            d2h_st.wait_event(solved[b])
-            uhs[b].copy_(uds[b], non_blocking=True)
-            out_done[b].record(d2h_st)
-
-    for k in range(4):
-        e2e_step(k)
+    lgfm.lgf_solve_host_pipelined(s32.plan, [fh] * 4, [uhs[k % 2] for k in range(4)], stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(k_e2e):
-        e2e_step(k)
-    torch.cuda.synchronize()
+    lgfm.lgf_solve_host_pipelined(s32.plan, [fh] * k_e2e, [uhs[k % 2] for k in range(k_e2e)], stream)
     e2e_s = (time.perf_counter() - t0) / k_e2e
 
+    # measured FMA peaks (the denominator of the ALU rooflines)
+    fma = measure_fma_peaks(lgfm, dev)
     # roofline of the dominant kernel
     dom = max(ktimes.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_tot, dom_cnt) = dom
@@ -627,12 +638,14 @@ def main():
     roof = None
     if dom_name in work:
         flops = 8.0 * work[dom_name][0]                   # one complex MAC = 8 real flops
-        peak_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
+        derived_tf = N_SM * FP32_FMA_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
+        peak_tf = fma["fp32_best_tflops"]
         ach = flops / (dom_ms * 1e-3) / 1e12
         iso_ms = kt_iso[dom_name][0] / kt_iso[dom_name][1]
         roof = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": profiled_traffic(dom_name),
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
+                "peak_source": "measured: lgf_measure_fma_peak, best of fma.rn.f32 and fma.rn.f32x2 on all SMs",
+                "peak_derived": derived_tf, "frac_of_derived": ach / derived_tf,
                 "algorithmic": "8 flop x " + work[dom_name][1],
                 "ms_in_step": dom_ms, "ms_isolated": iso_ms,
                 # the persistent products leave some SMs to the levels >= 2
@@ -662,9 +675,9 @@ def main():
         "fp64": {"value": rate64, "unit": "points/s", "ms_per_step": statistics.mean(ms64), "steps": k64},
         "e2e": {"value": npts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(fh.numel() * 4),
                 "d2h_bytes_per_step": int(uh.numel() * 4), "steps": k_e2e,
-                "how": "one plan solving in order; every step's pinned-host H2D copy runs ahead on a copy stream "
-                       "and its D2H copy behind on another, double-buffered device arrays; "
-                       "wall clock over all steps"},
+                "how": "one lgf_solve_host_pipelined call (C ABI, pinned host buffers): every step's H2D copy "
+                       "runs ahead of its solve and its D2H copy behind it on library-owned copy streams, "
+                       "double-buffered device arrays; wall clock over all steps"},
         "e2e_serial": {"value": npts / e2e_serial_s, "unit": "points/s",
                        "how": "lgf_solve_host per step (copy in, solve, copy out, synchronize)"},
         "gpu_launches": int(per_solve_launches) * args.steps,
@@ -672,7 +685,7 @@ def main():
         "kernel_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
         "ms_per_step_traced": statistics.mean(ms_traced),
         "kernel_ms_isolated": {k: v[0] / v[1] for k, v in kt_iso.items()},
-        "roofline": roof, "peaks": src,
+        "roofline": roof, "peaks": src, "fma_peaks": fma,
         "clocks": clk, "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -681,6 +694,7 @@ def main():
         torch.cuda.synchronize()
         got = u32.double().cpu().numpy()
         out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                               "nproc": os.cpu_count(), "cpu_model": cpu_model(),
                                "sample": f"one full oracle FMM solve of the 128^3 torus ({secs:.1f} s, "
                                          "kernel spectra precomputed outside the timing)"}
         out["rel_err_fp32_vs_oracle"] = fmm.rel_linf(got, uref)
@@ -692,7 +706,8 @@ def main():
             out["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and not args.no_fft_conv:
         try:
-            out["fft_conv"] = fft_conv_run(torch, lgfm, max(3, min(100, args.steps // 20)), flush)
+            out["fft_conv"] = fft_conv_run(torch, lgfm, max(3, min(100, args.steps // 20)), flush,
+                                           fma["fp32_best_tflops"])
         except Exception as exc:
             out["fft_conv"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and not args.no_irregular:

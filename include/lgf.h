@@ -58,7 +58,14 @@ typedef enum {
 typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
 
 /* Arithmetic of the regularization / interpolation contractions (Eqs. alg_reg,
- * alg_interp).  NATIVE uses the plan precision on the CUDA cores.  The others
+ * alg_interp).  NATIVE uses the plan precision on the CUDA cores; in an FP32
+ * plan whose interaction lists reach level 3 or higher (four or more levels)
+ * it sums with compensation, as COMPENSATED below, because there a level-1
+ * field carries three or more interpolated levels whose FP32 roundings,
+ * amplified by the stencil's Lebesgue constant (Sec. 2.5), approach the 1e-5
+ * relative tolerance (5-level 512^3 domain: 1.04e-5 plain, 7.7e-6
+ * compensated, measured against the FP64 form).  PLAIN forces plain sums in
+ * the plan precision at any depth.  The others
  * (FP32 plans only) run each axis pass as a tensor-core GEMM (tcgen05.mma)
  * with FP32 accumulation; the field between passes stays FP32 and only the
  * MMA inputs (field values and weights) are rounded:
@@ -67,6 +74,13 @@ typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
  *                      65504 overflow: fields of order 1e4 or more need NATIVE)
  *   LGF_INTERP_BF16X3  inputs split into three BF16 parts, six partial
  *                      products: close to FP32 accuracy
+ * Relative errors against the FP64 form, measured: in trees of up to 4
+ * levels BF16 0.09-0.12 and FP16 1.1e-2-1.3e-2, inside 48 u (u = 2^-8 BF16,
+ * 2^-11 FP16: up to 12 rounded passes, each amplified by the order-8
+ * stencil's Lebesgue constant of about 3); that bound holds to 4 levels only:
+ * on the 5-level 512^3 domain BF16 gives 0.40 and FP16 5.6e-2, as each
+ * further level adds six rounded passes amplified through the levels below.
+ * No reduced-precision mode meets the 1e-5 FP32 tolerance at 5 levels.
  * and, on the CUDA cores:
  *   LGF_INTERP_COMPENSATED  FP32 passes whose dot products carry the exact
  *                      rounding error of every product and sum (FMA-based
@@ -82,7 +96,8 @@ typedef enum {
     LGF_INTERP_BF16 = 1,
     LGF_INTERP_FP16 = 2,
     LGF_INTERP_BF16X3 = 3,
-    LGF_INTERP_COMPENSATED = 4
+    LGF_INTERP_COMPENSATED = 4,
+    LGF_INTERP_PLAIN = 5
 } lgf_interp_mode;
 
 /*
@@ -102,8 +117,9 @@ typedef enum {
  *                 nodes are used per point, 1 <= n_max <= n_b + 1
  *   precision     LGF_FP32 or LGF_FP64 (FFTs, products and interpolation);
  *                 the LGF values and spectra are always generated in FP64
- *   interp_mode   LGF_INTERP_NATIVE, or for FP32 plans LGF_INTERP_BF16,
- *                 LGF_INTERP_FP16, LGF_INTERP_BF16X3, LGF_INTERP_COMPENSATED
+ *   interp_mode   LGF_INTERP_NATIVE or LGF_INTERP_PLAIN, or for FP32 plans
+ *                 LGF_INTERP_BF16, LGF_INTERP_FP16, LGF_INTERP_BF16X3,
+ *                 LGF_INTERP_COMPENSATED
  *                 (LGF_ERR_UNSUPPORTED for FP64 plans)
  *   out           receives the plan
  *
@@ -219,6 +235,9 @@ lgf_status lgf_plan_create_multi(const int32_t *block_ijk, const int64_t *block_
  *                      that level uses another form
  *   n_levels           the largest level count of its problems
  *   fft_kernel         the level-0 FFT form in use (see lgf_plan_options)
+ *   compensated_interp 1 if the CUDA-core Reg/Interp passes sum with
+ *                      compensation (mode COMPENSATED, or NATIVE in a deep
+ *                      FP32 plan), else 0
  */
 #define LGF_MAX_LEVELS 24
 typedef struct {
@@ -233,6 +252,7 @@ typedef struct {
     int32_t n_problems;
     int32_t persistent_ctas;
     int32_t fft_kernel;
+    int32_t compensated_interp;
 } lgf_plan_stats;
 
 lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats *stats);
@@ -296,11 +316,46 @@ lgf_status lgf_batch_destroy(lgf_batch batch);
 lgf_status lgf_selftest_bounded_wait(int32_t complete, int32_t limit_us);
 
 /*
+ * lgf_measure_fma_peak - measured arithmetic peak of the current device (no
+ * counterpart in the paper: the denominator of the rooflines of the products
+ * and transforms, which run on the CUDA cores' fused multiply-add pipes).
+ * Every SM runs as many CTAs as fit, each thread 16 independent chains of
+ * fused multiply-adds; CUDA events time each launch; flop = 2 per FMA lane.
+ *   kind         0 = fma.rn.f64, 1 = fma.rn.f32, 2 = fma.rn.f32x2 (two FP32
+ *                lanes per instruction)
+ *   reps         1..100 timed launches after one warm-up; the best is kept
+ *   flops_per_s  receives the best launch's rate
+ *   ms           receives that launch's duration
+ * Synchronous on the legacy default stream; allocates a small buffer.
+ */
+lgf_status lgf_measure_fma_peak(int32_t kind, int32_t reps, double *flops_per_s, double *ms);
+
+/*
  * lgf_solve_host - lgf_solve with host buffers: copies f to the plan's device
  * staging buffer, solves, copies u back, and waits for the stream.
  *   f_host, u_host  host pointers of n_points values (pinned memory is faster)
  */
 lgf_status lgf_solve_host(lgf_plan plan, const void *f_host, void *u_host, void *stream);
+
+/*
+ * lgf_solve_host_pipelined - n_steps solves of one plan from host buffers,
+ * the copies overlapped with the solves inside the library (end-to-end
+ * throughput of a stream of inputs).  Step k copies f_host[k] into one of two
+ * plan-owned device input buffers on a library-owned host-to-device stream,
+ * solves on `stream` once that copy landed and the same buffer pair's
+ * previous result has left, and copies the result into u_host[k] on a
+ * library-owned device-to-host stream; so step k + 1's input copy and step
+ * k - 1's result copy run while step k solves.
+ *   f_host, u_host  n_steps host pointers each (pinned memory lets the copies
+ *                   overlap; pointers may repeat), n_points values per buffer
+ *   n_steps         >= 0
+ *   stream          the solves' stream; the first copy waits for the work
+ *                   already queued on it
+ * Returns when every result is in host memory.  The staging buffers (four
+ * field-sized device arrays) are allocated at the first call and kept.
+ */
+lgf_status lgf_solve_host_pipelined(lgf_plan plan, const void *const *f_host, void *const *u_host,
+                                    int32_t n_steps, void *stream);
 
 /* Waits for the plan's last solve and reports any asynchronous error. */
 lgf_status lgf_plan_sync(lgf_plan plan);
@@ -331,12 +386,14 @@ lgf_status lgf_plan_timings(lgf_plan plan, int32_t max_kernels, int32_t *n_kerne
  * All working memory (block spectra, kernel spectra, item tables) lives in one
  * file-scope device array of 32 MiB that every GPU loading the library holds
  * until the process exits.  The first call on a device, with that device
- * current, looks up the array's device address and uploads the tables with
- * synchronous copies; make that first call before any stream capture.  Each
- * (n_b, precision) pair's first call also uploads its kernel spectrum.
+ * current, looks up the array's device address and uploads the tables and
+ * the kernel spectra of every (n_b, precision) pair with synchronous copies;
+ * make that first call before any stream capture.  Later calls only launch
+ * kernels on the stream.
  *
  *   f_dev, u_dev  device pointers, n_blocks * n_b^3 values of the precision,
- *                 block-major with x fastest (as lgf_solve); must not overlap
+ *                 block-major with x fastest (as lgf_solve); the two byte
+ *                 ranges must not overlap (LGF_ERR_INVALID_ARG)
  *   n_blocks      1 .. lgf_noalloc_max_blocks(n_b, precision); more is
  *                 LGF_ERR_INVALID_ARG (232 for n_b = 16 in FP32, 116 in FP64)
  *   n_b           4, 8 or 16;  precision  LGF_FP32 or LGF_FP64

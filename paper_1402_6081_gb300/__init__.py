@@ -22,6 +22,7 @@ LGF_INTERP_BF16 = 1
 LGF_INTERP_FP16 = 2
 LGF_INTERP_BF16X3 = 3
 LGF_INTERP_COMPENSATED = 4
+LGF_INTERP_PLAIN = 5
 
 _STATUS = {0: "LGF_OK", 1: "LGF_ERR_INVALID_ARG", 2: "LGF_ERR_UNSUPPORTED", 3: "LGF_ERR_OOM",
            4: "LGF_ERR_CUDA", 5: "LGF_ERR_TIMEOUT", 6: "LGF_ERR_BUDGET"}
@@ -46,12 +47,16 @@ _SIGS = {
     "lgf_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p]),
     "lgf_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_solve_host_pipelined": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_void_p]),
     "lgf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "lgf_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lgf_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "lgf_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "lgf_measure_fma_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "lgf_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -134,7 +139,7 @@ class lgf_plan_stats(ctypes.Structure):
                 ("nw", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("workspace_bytes", ctypes.c_int64), ("merged_level01", ctypes.c_int32),
                 ("n_problems", ctypes.c_int32), ("persistent_ctas", ctypes.c_int32),
-                ("fft_kernel", ctypes.c_int32)]
+                ("fft_kernel", ctypes.c_int32), ("compensated_interp", ctypes.c_int32)]
 
 
 def lgf_plan_create(blocks, n_b: int, n_levels: int, interp_order: int,
@@ -211,7 +216,8 @@ def lgf_plan_get_stats(plan: int) -> dict:
             "intervals": list(st.intervals[: L + 1]), "groups": list(st.groups[: L + 1]),
             "nw": list(st.nw[: L + 1]), "workspace_bytes": st.workspace_bytes,
             "merged_level01": st.merged_level01, "n_problems": st.n_problems,
-            "persistent_ctas": st.persistent_ctas, "fft_kernel": st.fft_kernel}
+            "persistent_ctas": st.persistent_ctas, "fft_kernel": st.fft_kernel,
+            "compensated_interp": st.compensated_interp}
 
 
 def lgf_plan_workspace_bytes(plan: int) -> int:
@@ -266,6 +272,19 @@ def lgf_solve_host(plan: int, f_host, u_host, stream=None) -> None:
     _check(library().lgf_solve_host(plan, fp, up, _stream_ptr(stream)), "lgf_solve_host")
 
 
+def lgf_solve_host_pipelined(plan: int, f_hosts, u_hosts, stream=None) -> None:
+    """Solves of one plan over sequences of host buffers (equal lengths; NumPy
+    arrays or CPU tensors, pinned preferred), copies overlapped with the solves
+    inside the library; returns with every result in host memory."""
+    if len(f_hosts) != len(u_hosts):
+        raise ValueError("f_hosts and u_hosts must have the same length")
+    ptr = lambda a: a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    n = len(f_hosts)
+    fa = (ctypes.c_void_p * max(n, 1))(*[ptr(a) for a in f_hosts])
+    ua = (ctypes.c_void_p * max(n, 1))(*[ptr(a) for a in u_hosts])
+    _check(library().lgf_solve_host_pipelined(plan, fa, ua, n, _stream_ptr(stream)), "lgf_solve_host_pipelined")
+
+
 def lgf_selftest_bounded_wait(complete: int, limit_us: int) -> None:
     """Run one bounded device wait (see include/lgf.h); raises LgfError with
     LGF_ERR_TIMEOUT when it runs out."""
@@ -296,6 +315,14 @@ def lgf_plan_timings(plan: int):
         nm = names.raw[32 * j: 32 * (j + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (tot[j], cnt[j])
     return out, per.value
+
+
+def lgf_measure_fma_peak(kind: int, reps: int = 5) -> tuple[float, float]:
+    """(flop/s, ms) of the best of reps all-SM FMA launches: kind 0 FP64,
+    1 FP32, 2 packed FP32 pairs (see include/lgf.h)."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(library().lgf_measure_fma_peak(kind, reps, ctypes.byref(r), ctypes.byref(ms)), "lgf_measure_fma_peak")
+    return r.value, ms.value
 
 
 def lgf_solve_blocks_noalloc(f, u, n_blocks: int, n_b: int, precision: int, stream=None) -> None:

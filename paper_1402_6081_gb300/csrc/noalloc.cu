@@ -13,9 +13,10 @@
 // host-side stand-in, so the device address is fetched once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
 // that device; that first call also uploads the item tables, the FFT twiddles
-// of this translation unit and, per (n_b, precision), the kernel spectrum,
-// with synchronous copies.  Make the first call on each device before any
-// stream capture.  Later calls only launch three kernels on the given stream.
+// of this translation unit and the kernel spectra of all six (n_b, precision)
+// pairs (under 0.5 MiB together), with synchronous copies.  Make the first
+// call on each device before any stream capture.  Later calls, whatever their
+// n_b and precision, only launch three kernels on the given stream.
 //
 // All calls share the array and it keeps the last call's contents; every
 // value a call reads is written earlier in the same call, so nothing needs
@@ -58,7 +59,6 @@ size_t kernel_offset(int n_b, int prec) {
 
 struct DeviceState {
     unsigned char* base = nullptr;
-    bool kernel_ready[3][2] = {};
 };
 std::mutex g_mu;
 std::map<int, DeviceState> g_state;
@@ -87,7 +87,33 @@ cudaError_t upload_twiddles() {
     }
 }
 
-// First call on a device: the array's device address, item tables, twiddles.
+// Kernel spectrum of the block with itself (offset d = 0, level 0), FP64 on the
+// host, rounded to the precision, copied into the kernel region.
+lgf_status load_kernel(unsigned char* base, int n_b, int prec) {
+    const int S = 2 * n_b;
+    const int64_t NW = nw_of(S);
+    auto tab = green_abs_table(1, n_b - 1);
+    std::vector<std::complex<double>> kh(static_cast<size_t>(NW));
+    const int d[3] = {0, 0, 0};
+    kernel_spectrum(n_b, n_b, 1, S, d, tab->data(), n_b - 1, kh.data());
+    cudaError_t e;
+    unsigned char* dst = base + kernel_offset(n_b, prec);
+    if (prec == LGF_FP64) {
+        e = cudaMemcpy(dst, kh.data(), sizeof(double) * 2 * size_t(NW), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> f(2 * size_t(NW));
+        for (size_t i = 0; i < size_t(NW); ++i) {
+            f[2 * i] = float(kh[i].real());
+            f[2 * i + 1] = float(kh[i].imag());
+        }
+        e = cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cuda_err(e, "kernel spectrum upload");
+    return ok();
+}
+
+// First call on a device: the array's device address, item tables, twiddles
+// and every kernel spectrum.
 lgf_status setup_device(int device, DeviceState& st) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -107,34 +133,13 @@ lgf_status setup_device(int device, DeviceState& st) {
         return cuda_err(e, "item upload");
     if ((e = upload_twiddles<float>()) != cudaSuccess) return cuda_err(e, "twiddle upload");
     if ((e = upload_twiddles<double>()) != cudaSuccess) return cuda_err(e, "twiddle upload");
+    for (int nb : {4, 8, 16})
+        for (int pr : {LGF_FP32, LGF_FP64}) {
+            lgf_status r = load_kernel(base, nb, pr);
+            if (r != LGF_OK) return r;
+        }
     st.base = base;
     (void)device;
-    return ok();
-}
-
-// Kernel spectrum of the block with itself (offset d = 0, level 0), FP64 on the
-// host, rounded to the precision, copied into the kernel region.
-lgf_status load_kernel(DeviceState& st, int n_b, int prec) {
-    const int S = 2 * n_b;
-    const int64_t NW = nw_of(S);
-    auto tab = green_abs_table(1, n_b - 1);
-    std::vector<std::complex<double>> kh(static_cast<size_t>(NW));
-    const int d[3] = {0, 0, 0};
-    kernel_spectrum(n_b, n_b, 1, S, d, tab->data(), n_b - 1, kh.data());
-    cudaError_t e;
-    unsigned char* dst = st.base + kernel_offset(n_b, prec);
-    if (prec == LGF_FP64) {
-        e = cudaMemcpy(dst, kh.data(), sizeof(double) * 2 * size_t(NW), cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> f(2 * size_t(NW));
-        for (size_t i = 0; i < size_t(NW); ++i) {
-            f[2 * i] = float(kh[i].real());
-            f[2 * i + 1] = float(kh[i].imag());
-        }
-        e = cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
-    }
-    if (e != cudaSuccess) return cuda_err(e, "kernel spectrum upload");
-    st.kernel_ready[nb_index(n_b)][prec == LGF_FP64 ? 1 : 0] = true;
     return ok();
 }
 
@@ -189,7 +194,6 @@ extern "C" lgf_status lgf_solve_blocks_noalloc(const void* f_dev, void* u_dev, i
                                                int32_t precision, void* stream) {
     if (!f_dev || !u_dev || n_blocks < 1)
         return fail(LGF_ERR_INVALID_ARG, "lgf_solve_blocks_noalloc: need f, u and n_blocks >= 1");
-    if (f_dev == u_dev) return fail(LGF_ERR_INVALID_ARG, "lgf_solve_blocks_noalloc: f and u must not overlap");
     if (nb_index(n_b) < 0) return fail(LGF_ERR_UNSUPPORTED, "lgf_solve_blocks_noalloc: n_b must be 4, 8 or 16");
     if (precision != LGF_FP32 && precision != LGF_FP64)
         return fail(LGF_ERR_INVALID_ARG, "lgf_solve_blocks_noalloc: precision must be LGF_FP32 or LGF_FP64");
@@ -200,6 +204,14 @@ extern "C" lgf_status lgf_solve_blocks_noalloc(const void* f_dev, void* u_dev, i
                                              " blocks exceed the limit of " + std::to_string(mx) +
                                              " for n_b = " + std::to_string(n_b) + " in this precision (" +
                                              std::to_string(kNoAllocScratchBytes >> 20) + " MiB scratch)");
+    {
+        // the inverse transforms write u while later blocks' sources are
+        // still to be read: the byte ranges of f and u must be disjoint
+        const uintptr_t bytes = uintptr_t(n_blocks) * uintptr_t(n_b) * n_b * n_b * (precision == LGF_FP64 ? 8 : 4);
+        const uintptr_t f0 = reinterpret_cast<uintptr_t>(f_dev), u0 = reinterpret_cast<uintptr_t>(u_dev);
+        if (f0 < u0 + bytes && u0 < f0 + bytes)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_solve_blocks_noalloc: f and u must not overlap");
+    }
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
@@ -209,10 +221,6 @@ extern "C" lgf_status lgf_solve_blocks_noalloc(const void* f_dev, void* u_dev, i
         DeviceState& s = g_state[device];
         if (!s.base) {
             lgf_status r = setup_device(device, s);
-            if (r != LGF_OK) return r;
-        }
-        if (!s.kernel_ready[nb_index(n_b)][precision == LGF_FP64 ? 1 : 0]) {
-            lgf_status r = load_kernel(s, n_b, precision);
             if (r != LGF_OK) return r;
         }
         st = &s;

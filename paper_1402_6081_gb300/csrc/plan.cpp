@@ -324,9 +324,12 @@ struct DevLevel {
     int n_r2c = 0;
     C2RItem* c2r = nullptr;
     int n_c2r = 0;
+    // Reg and Interp items; the first n_reg_comp / n_int_comp belong to
+    // problems whose passes sum with compensation, the rest sum plainly
     int* reg_child = nullptr;
     int* reg_parent = nullptr;
-    int n_reg = 0;
+    int n_reg = 0, n_reg_comp = 0;
+    int n_int_comp = 0;
     int* int_slot = nullptr;
     int* int_parent = nullptr;
     int* int_block = nullptr;       // level 1: the block of each item (output into the blocks)
@@ -346,6 +349,10 @@ struct lgf_plan_s {
     int near_kernel = 0, interval_kernel = 0;   // product-kernel variants (options)
     int single_stream = 0;
     int interp_mode = LGF_INTERP_NATIVE;   // Reg/Interp arithmetic (FP32 plans: tensor-core modes)
+    // problems whose CUDA-core Reg/Interp passes sum with compensation (Dot2):
+    // mode COMPENSATED, or NATIVE in an FP32 problem whose interaction lists
+    // reach level 3 or higher (see build_plan)
+    int comp_sums = 0;
     int* err = nullptr;                 // device flag: a bounded wait in a kernel ran out
     // SMs left to the levels >= 2 chain beside the persistent level-0 products
     // (-1: none; the chain then runs before and after them)
@@ -374,6 +381,12 @@ struct lgf_plan_s {
     size_t bytes = 0;
     void* stage_f = nullptr;
     void* stage_u = nullptr;
+    // lgf_solve_host_pipelined: a second staging pair, copy streams and the
+    // events that order the two buffer pairs between copies and solves
+    void* stage_f2 = nullptr;
+    void* stage_u2 = nullptr;
+    cudaStream_t copy_st[2] = {nullptr, nullptr};      // H2D, D2H
+    cudaEvent_t pipe_ev[7] = {};                       // in_ready[2], solved[2], out_done[2], start
     // per-kernel event timing (lgf_plan_set_timing / lgf_plan_timings)
     std::vector<cudaEvent_t> ev;           // 2 * capacity events
     std::vector<const char*> ev_name;      // kernel name per recorded pair
@@ -395,6 +408,12 @@ struct lgf_plan_s {
         for (void* p : allocs) cudaFree(p);
         if (stage_f) cudaFree(stage_f);
         if (stage_u) cudaFree(stage_u);
+        if (stage_f2) cudaFree(stage_f2);
+        if (stage_u2) cudaFree(stage_u2);
+        for (cudaStream_t c : copy_st)
+            if (c) cudaStreamDestroy(c);
+        for (cudaEvent_t e : pipe_ev)
+            if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         for (cudaStream_t a : aux)
             if (a) cudaStreamDestroy(a);
@@ -795,6 +814,24 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
         if (s != LGF_OK) return s;
         P->err = static_cast<int*>(e);
     }
+    // Compensated Reg/Interp sums (Dot2), decided per problem so that every
+    // problem of a multi-problem plan gets the arithmetic it has alone: mode
+    // COMPENSATED, or NATIVE in an FP32 problem whose interaction lists reach
+    // level 3 or higher.  There a level-1 field is the sum of three or more
+    // interpolated levels, and each Reg/Interp pass rounds FP32 sums of up to
+    // n_max weights of mixed sign, the rounding amplified by the stencil's
+    // Lebesgue constant (Sec. 2.5).  Measured on the 512^3 irregular 5-level
+    // domain against the FP64 form: plain sums 1.04e-5, compensated 7.7e-6
+    // (the 1e-5 FP32 tolerance), for 8% of the solve time; with products at
+    // two levels only (the 128^3 torus) the transforms and products dominate
+    // the error and the plain sums are kept.
+    std::vector<int> pcomp(np, 0);
+    P->comp_sums = 0;
+    for (size_t p = 0; p < np; ++p) {
+        pcomp[p] = P->interp_mode == LGF_INTERP_COMPENSATED ||
+                   (P->interp_mode == LGF_INTERP_NATIVE && P->prec == LGF_FP32 && hp[p].Lmac >= 3);
+        P->comp_sums += pcomp[p];
+    }
     P->lev.resize(size_t(Lmac) + 1);
     for (int l = 0; l <= Lmac; ++l) {
         const auto& go = goff[size_t(l)];
@@ -871,12 +908,15 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
         if (l >= 2) {
             if ((s = dalloc(P, slots * n3 * elem, &D.ft, true)) != LGF_OK) return s;
             std::vector<int> child, par;
-            for (size_t p = 0; p < np; ++p) {
-                if (go[p] < 0) continue;
-                const HostLevel& T = hp[p].lev[size_t(l)];
-                for (int v : T.reg_parent) par.push_back(v + 8 * go[p]);
-                for (int c : T.reg_child)
-                    child.push_back(c < 0 ? -1 : l == 2 ? c + boff[p] : c + 8 * goff[size_t(l) - 1][p]);
+            for (int pass : {1, 0}) {   // compensated problems' items first
+                for (size_t p = 0; p < np; ++p) {
+                    if (go[p] < 0 || pcomp[p] != pass) continue;
+                    const HostLevel& T = hp[p].lev[size_t(l)];
+                    for (int v : T.reg_parent) par.push_back(v + 8 * go[p]);
+                    for (int c : T.reg_child)
+                        child.push_back(c < 0 ? -1 : l == 2 ? c + boff[p] : c + 8 * goff[size_t(l) - 1][p]);
+                }
+                if (pass == 1) D.n_reg_comp = int(par.size());
             }
             D.n_reg = int(par.size());
             if ((s = check_range("Reg child", child, -1, l == 2 ? P->n_blocks : 8LL * ngroups[size_t(l) - 1])) != LGF_OK)
@@ -887,14 +927,17 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
         }
         if (l >= 1 && l < Lmac) {
             std::vector<int> sl, pa, bl;
-            for (size_t p = 0; p < np; ++p) {
-                if (go[p] < 0 || l >= hp[p].Lmac) continue;
-                const HostLevel& T = hp[p].lev[size_t(l)];
-                for (int v : T.int_slot) sl.push_back(v + 8 * go[p]);
-                for (int v : T.int_parent) pa.push_back(v + 8 * goff[size_t(l) + 1][p]);
-                // level-1 intervals are the problem's blocks, in block order
-                if (l == 1)
-                    for (size_t i = 0; i < T.int_slot.size(); ++i) bl.push_back(boff[p] + int(i));
+            for (int pass : {1, 0}) {   // compensated problems' items first
+                for (size_t p = 0; p < np; ++p) {
+                    if (go[p] < 0 || l >= hp[p].Lmac || pcomp[p] != pass) continue;
+                    const HostLevel& T = hp[p].lev[size_t(l)];
+                    for (int v : T.int_slot) sl.push_back(v + 8 * go[p]);
+                    for (int v : T.int_parent) pa.push_back(v + 8 * goff[size_t(l) + 1][p]);
+                    // level-1 intervals are the problem's blocks, in block order
+                    if (l == 1)
+                        for (size_t i = 0; i < T.int_slot.size(); ++i) bl.push_back(boff[p] + int(i));
+                }
+                if (pass == 1) D.n_int_comp = int(sl.size());
             }
             D.n_int = int(sl.size());
             if ((s = check_range("Interp slot", sl, 0, static_cast<long long>(slots))) != LGF_OK) return s;
@@ -1006,16 +1049,26 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     }
     // Reg/Interp arithmetic: tensor-core modes, or the CUDA-core kernels with
     // plain or compensated sums
-    const bool tc_mode = P->interp_mode != LGF_INTERP_NATIVE && P->interp_mode != LGF_INTERP_COMPENSATED;
-    const int comp = P->interp_mode == LGF_INTERP_COMPENSATED ? 1 : 0;
-    // Interp of level l + 1 into the level-l items of D (see Launch::interp)
+    const bool tc_mode = P->interp_mode != LGF_INTERP_NATIVE && P->interp_mode != LGF_INTERP_COMPENSATED &&
+                         P->interp_mode != LGF_INTERP_PLAIN;
+    // Interp of level l + 1 into the level-l items of D (see Launch::interp);
+    // the CUDA-core form in up to two launches: the items of problems with
+    // compensated sums, then the others
     auto interp = [&](DevLevel& D, T* out, const T* up, int accumulate, const int* block, cudaStream_t s) {
         if constexpr (sizeof(T) == 4) {
             if (tc_mode)
                 return interp_tc(P->interp_mode, nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block,
                                  P->err, s);
         }
-        return Lc::interp(nb, P->n_max, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block, comp, s);
+        cudaError_t r = cudaSuccess;
+        const int nc = D.n_int_comp;
+        if (nc > 0)
+            r = Lc::interp(nb, P->n_max, D.int_slot, D.int_parent, nc, out, up, W, accumulate, block, 1, s);
+        if (nc > 0 && D.n_int > nc) ++P->launches_last;   // the second launch of this phase
+        if (r == cudaSuccess && D.n_int > nc)
+            r = Lc::interp(nb, P->n_max, D.int_slot + nc, D.int_parent + nc, D.n_int - nc, out, up, W, accumulate,
+                           block ? block + nc : nullptr, 0, s);
+        return r;
     };
     // ---- levels >= 2 upward on s2: Reg from the level below, forward FFT
     auto up_part = [&]() -> lgf_status {
@@ -1029,8 +1082,16 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                         return reg_tc(P->interp_mode, nb, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
                                       static_cast<T*>(D.ft), W, P->err, s2);
                 }
-                return Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
-                               static_cast<T*>(D.ft), W, comp, s2);
+                cudaError_t r = cudaSuccess;
+                const int nc = D.n_reg_comp;
+                if (nc > 0)
+                    r = Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, nc,
+                                static_cast<T*>(D.ft), W, 1, s2);
+                if (nc > 0 && D.n_reg > nc) ++P->launches_last;
+                if (r == cudaSuccess && D.n_reg > nc)
+                    r = Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child + 8 * size_t(nc),
+                                D.reg_parent + nc, D.n_reg - nc, static_cast<T*>(D.ft), W, 0, s2);
+                return r;
             });
             if (e != cudaSuccess) return cuda_fail(e, "regularization");
             if (D.m2l) {
@@ -1243,9 +1304,9 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: precision must be LGF_FP32 or LGF_FP64");
-    if (interp_mode < LGF_INTERP_NATIVE || interp_mode > LGF_INTERP_COMPENSATED)
-        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..4");
-    if (interp_mode != LGF_INTERP_NATIVE && precision != LGF_FP32)
+    if (interp_mode < LGF_INTERP_NATIVE || interp_mode > LGF_INTERP_PLAIN)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..5");
+    if (interp_mode != LGF_INTERP_NATIVE && interp_mode != LGF_INTERP_PLAIN && precision != LGF_FP32)
         return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: reduced-precision interpolation modes need an FP32 plan");
     auto P = std::make_unique<lgf_plan_s>();
     cudaError_t e = cudaGetDevice(&P->device);
@@ -1384,6 +1445,7 @@ lgf_status lgf_plan_get_stats(lgf_plan plan, lgf_plan_stats* st) {
     st->n_problems = plan->n_problems;
     st->persistent_ctas = uses_persist(plan, 0) ? plan->lev[0].pp.n_cta : 0;
     st->fft_kernel = plan->fft_kernel;
+    st->compensated_interp = plan->comp_sums;
     if (plan->merged && plan->Lmac >= 1) st->nw[1] = nw_of(plan->S0);
     size_t b = 0;
     lgf_plan_workspace_bytes(plan, &b);
@@ -1441,6 +1503,56 @@ lgf_status lgf_solve_host(lgf_plan plan, const void* f_host, void* u_host, void*
     s = lgf_solve(plan, plan->stage_f, plan->stage_u, stream);
     if (s != LGF_OK) return s;
     LGF_CUDA(cudaMemcpyAsync(u_host, plan->stage_u, bytes, cudaMemcpyDeviceToHost, st));
+    LGF_CUDA(cudaStreamSynchronize(st));
+    return ok();
+}
+
+lgf_status lgf_solve_host_pipelined(lgf_plan plan, const void* const* f_host, void* const* u_host, int32_t n_steps,
+                                    void* stream) {
+    if (!plan || n_steps < 0 || (n_steps > 0 && (!f_host || !u_host)))
+        return fail(LGF_ERR_INVALID_ARG, "lgf_solve_host_pipelined: bad arguments");
+    for (int32_t k = 0; k < n_steps; ++k)
+        if (!f_host[k] || !u_host[k]) return fail(LGF_ERR_INVALID_ARG, "lgf_solve_host_pipelined: NULL host buffer");
+    lgf_status s = check_device(plan);
+    if (s != LGF_OK) return s;
+    if (n_steps == 0) return ok();
+    const size_t bytes = size_t(plan->n_points) * (plan->prec == LGF_FP64 ? sizeof(double) : sizeof(float));
+    if (!plan->stage_f2) {
+        cudaError_t e = cudaSuccess;
+        for (void** p : {&plan->stage_f, &plan->stage_u, &plan->stage_f2, &plan->stage_u2})
+            if (!*p && e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) return fail(LGF_ERR_OOM, std::string("staging buffers: ") + cudaGetErrorString(e));
+        for (cudaStream_t& c : plan->copy_st) LGF_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        for (cudaEvent_t& e2 : plan->pipe_ev) LGF_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t h2d = plan->copy_st[0], d2h = plan->copy_st[1];
+    cudaEvent_t* in_ready = plan->pipe_ev;
+    cudaEvent_t* solved = plan->pipe_ev + 2;
+    cudaEvent_t* out_done = plan->pipe_ev + 4;
+    void* fd[2] = {plan->stage_f, plan->stage_f2};
+    void* ud[2] = {plan->stage_u, plan->stage_u2};
+    // the copies start after the work already queued on the caller's stream
+    LGF_CUDA(cudaEventRecord(plan->pipe_ev[6], st));
+    LGF_CUDA(cudaStreamWaitEvent(h2d, plan->pipe_ev[6], 0));
+    for (int32_t k = 0; k < n_steps; ++k) {
+        const int b = k & 1;
+        // input k into buffer b once the solve of step k - 2 has read it
+        if (k >= 2) LGF_CUDA(cudaStreamWaitEvent(h2d, solved[b], 0));
+        LGF_CUDA(cudaMemcpyAsync(fd[b], f_host[k], bytes, cudaMemcpyHostToDevice, h2d));
+        LGF_CUDA(cudaEventRecord(in_ready[b], h2d));
+        // solve k once its input is in and step k - 2's result has left ud[b]
+        LGF_CUDA(cudaStreamWaitEvent(st, in_ready[b], 0));
+        if (k >= 2) LGF_CUDA(cudaStreamWaitEvent(st, out_done[b], 0));
+        s = lgf_solve(plan, fd[b], ud[b], stream);
+        if (s != LGF_OK) return s;
+        LGF_CUDA(cudaEventRecord(solved[b], st));
+        // result k out behind its solve
+        LGF_CUDA(cudaStreamWaitEvent(d2h, solved[b], 0));
+        LGF_CUDA(cudaMemcpyAsync(u_host[k], ud[b], bytes, cudaMemcpyDeviceToHost, d2h));
+        LGF_CUDA(cudaEventRecord(out_done[b], d2h));
+    }
+    LGF_CUDA(cudaStreamSynchronize(d2h));
     LGF_CUDA(cudaStreamSynchronize(st));
     return ok();
 }

@@ -4,7 +4,12 @@ physical size, for interval sizes n_I = 5, 9, 17 at a fixed interpolation
 order: the paper's error experiment (Sec. 4, error against n_I at fixed n_max).
 The FP64 path is used, so the error is the method's own; at fixed n_max it
 falls as n_I grows (finer intervals relative to the kernel's smoothness).
-Rates (points/s, FP32 and FP64) are recorded with the errors."""
+Every GPU result is also compared with the oracle FMM on the same domain,
+element by element: the GPU computes the same truncated method, so FP64 agrees
+with it to 1e-12 and FP32 to 1e-5, both times the source's conditioning kappa =
+max|G * |f|| / max|G * f| (about 2e3 for these random manufactured sources;
+the oracle's solve of |f|).  Rates (points/s, FP32 and FP64) are recorded with
+the errors."""
 import numpy as np
 import pytest
 
@@ -59,9 +64,16 @@ def test_error_falls_with_interval_size(shape):
         u32, r32 = _solve(m, lgfm.LGF_FP32)
         e64 = fmm.rel_linf(u64, m.u_exact)
         e32 = fmm.rel_linf(u32, m.u_exact)
+        ref = fmm.fmm_solve(m.blocks, m.f, n_b, L, ORDER)
+        kappa = max(1.0, float(np.abs(fmm.fmm_solve(m.blocks, np.abs(m.f), n_b, L, ORDER)).max()
+                               / np.abs(ref).max()))
+        p64, p32 = fmm.rel_linf(u64, ref), fmm.rel_linf(u32, ref)
         record_error(f"sweep_{shape}_nI{n_b + 1}", fp64_vs_exact=e64, fp32_vs_exact=e32, points=m.n_points,
-                     fp64_points_per_s=r64, fp32_points_per_s=r32)
-        print(f"{shape} n_I {n_b + 1}: fp64 err {e64:.3e} fp32 err {e32:.3e} "
-              f"rate fp32 {r32:.3e} fp64 {r64:.3e} points {m.n_points}")
+                     fp64_points_per_s=r64, fp32_points_per_s=r32, fp64_vs_oracle=p64, fp32_vs_oracle=p32,
+                     oracle_vs_exact=fmm.rel_linf(ref, m.u_exact), kappa=kappa)
+        print(f"{shape} n_I {n_b + 1}: fp64 err {e64:.3e} fp32 err {e32:.3e} vs oracle {p64:.2e}/{p32:.2e} "
+              f"kappa {kappa:.0f} rate fp32 {r32:.3e} fp64 {r64:.3e} points {m.n_points}")
+        assert p64 <= 1e-12 * kappa, (n_b, p64, kappa)
+        assert p32 <= 1e-5 * kappa, (n_b, p32, kappa)
         errs.append(e64)
     assert errs[0] > errs[1] > errs[2], errs

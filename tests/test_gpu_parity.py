@@ -9,11 +9,15 @@ rounding of a convolution scales with sum |G||f|, not with |u|.  G < 0
 everywhere, so G * |f| is the oracle's own solve of |f|.  kappa = 1 for every
 non-negative source (all the benchmark workloads), where the bounds are the
 plain 1e-12 and 1e-5; a random manufactured source (the Laplacian of noise)
-has kappa ~ 2e3.  Where the method involves no interpolation the oracle FMM
-itself equals the exact direct sum, so the same bounds hold against it.
+has kappa ~ 2e3 (its u is three orders of magnitude below the terms summed
+into it: FP64 errors of 6.6e-12 relative to max|u| there are 2.8e-15 relative
+to max|G * |f||).  Every such case records the plain error beside kappa, and
+plain-tolerance cases with signed, smooth sources of small kappa (a dipole of
+two Gaussians) and with the non-negative 5-level irregular domain hold the
+plain 1e-12 / 1e-5 with no factor.  Where the method involves no
+interpolation the oracle FMM itself equals the exact direct sum, so the same
+bounds hold against it.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -67,14 +71,17 @@ def kappa(p):
     return max(1.0, float(np.abs(ua).max() / np.abs(oracle_u(p)).max()))
 
 
-def check(p, tol64=TOL64, tol32=TOL32):
+def check(p, tol64=TOL64, tol32=TOL32, plain=False):
+    """GPU FP64 and FP32 against the oracle; bounds scaled by kappa unless
+    plain (then kappa is only recorded)."""
     ref = oracle_u(p)
     k = kappa(p)
     e64 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP64), ref)
     e32 = fmm.rel_linf(gpu_solve(p, lgfm.LGF_FP32), ref)
     record_error(p.name, fp64_vs_oracle=e64, fp32_vs_oracle=e32, kappa=k)
-    assert e64 <= tol64 * k, ("fp64", e64, k)
-    assert e32 <= tol32 * k, ("fp32", e32, k)
+    scale = 1.0 if plain else k
+    assert e64 <= tol64 * scale, ("fp64", e64, k)
+    assert e32 <= tol32 * scale, ("fp32", e32, k)
     return e64, e32
 
 
@@ -141,6 +148,16 @@ def test_far_blocks_only_upper_level_interacts():
 def test_deep_tree_nb4_five_levels():
     m = W.manufactured(W.full_box_blocks(16, 8, 8), 4, 5, 4, seed=3)
     check(m)
+
+
+@pytest.mark.parametrize("nb,n_b,sigma,sep,L", [(8, 8, 4.0, 16.0, 3), (16, 8, 6.0, 24.0, 4), (8, 16, 6.0, 24.0, 3)])
+def test_signed_dipole_plain_tolerance(nb, n_b, sigma, sep, L):
+    # a smooth signed source (two Gaussians of opposite sign) at depth >= 3:
+    # small kappa, so the plain bounds apply with no conditioning factor
+    p = W.dipole_box(nb=nb, n_b=n_b, sigma=sigma, sep=sep, n_levels=L)
+    k = kappa(p)
+    assert k < 3.0, k
+    check(p, plain=True)
 
 
 _variant_problem = None
@@ -265,45 +282,54 @@ def irregular():
 
 
 def test_irregular_512_fp32_vs_fp64(irregular):
-    # Five levels: FP32 rounding noise of the fields at levels >= 2 reaches the
-    # leaves through up to three interpolations, and the one-sided 9-node
-    # stencils at interval ends amplify noise by their Lebesgue constant
-    # (Sec. 2.5: perturbations grow by Lambda^3 in 3D; with n_max = 9 the bound
-    # Lambda^3 * eps_fp32 is ~1e-3).  A float32 emulation of the oracle shows
-    # the same error (it comes from the products, inverse FFTs and
-    # interpolation of levels >= 2).  Measured: 1.1e-5 at this depth, above
-    # the 1e-5 target; 5.7e-6 at three levels (test_torus_128_three_levels).
-    # The compensated interpolation mode sums each Reg/Interp pass in twice
-    # the working precision (rounded once per pass), which removes the
-    # interpolation sums' share of that error and meets the 1e-5 contract.
+    # Five levels, FP32 against the FP64 form (kappa = 1, non-negative source).
+    # FP32 rounding of the fields at levels >= 2 reaches the leaves through up
+    # to three interpolations, and the stencils amplify it by their Lebesgue
+    # constant (Sec. 2.5).  With plain FP32 sums in Reg/Interp this deep tree
+    # measures 1.04e-5, just above the 1e-5 tolerance; the library's default
+    # for FP32 plans whose interaction lists reach level 3 sums every Reg/Interp
+    # pass with compensation (twice the working precision, rounded once per
+    # pass), which meets it.
     p = irregular
     u64 = gpu_solve(p, lgfm.LGF_FP64)
-    u32 = gpu_solve(p, lgfm.LGF_FP32)
-    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, interp_mode=lgfm.LGF_INTERP_COMPENSATED)
-    uc = s(torch.from_numpy(p.f).float().cuda())
-    lgfm.lgf_plan_sync(s.plan)
-    uc = uc.double().cpu().numpy()
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    assert s.stats()["compensated_interp"] == 1
     s.close()
-    e32, ec = fmm.rel_linf(u32, u64), fmm.rel_linf(uc, u64)
-    record_error("tori_irregular_512", fp32_vs_fp64=e32, fp32_compensated_vs_fp64=ec)
-    assert e32 <= 2e-5          # kappa = 1 (non-negative source)
-    assert ec <= 1e-5 and ec < e32
+    u32 = gpu_solve(p, lgfm.LGF_FP32)
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, interp_mode=lgfm.LGF_INTERP_PLAIN)
+    assert s.stats()["compensated_interp"] == 0
+    up = s(torch.from_numpy(p.f).float().cuda())
+    lgfm.lgf_plan_sync(s.plan)
+    up = up.double().cpu().numpy()
+    s.close()
+    e32, ep = fmm.rel_linf(u32, u64), fmm.rel_linf(up, u64)
+    record_error("tori_irregular_512", fp32_vs_fp64=e32, fp32_plain_sums_vs_fp64=ep)
+    assert e32 <= TOL32
     assert np.all(np.isfinite(u64)) and np.abs(u64).max() > 0
 
 
-@pytest.mark.skipif(not os.environ.get("LGF_FULL_ORACLE"),
-                    reason="full 512^3 oracle run (~3 min of CPU); set LGF_FULL_ORACLE=1")
-def test_irregular_512_full_oracle(irregular):
-    # element-by-element parity with the oracle at full size (7252 blocks, 3e7 points)
-    check(irregular)
+def test_tori_subset_five_levels_vs_oracle(irregular):
+    # element-by-element parity with the oracle at 5 levels and n_b = 16: an
+    # 8% seeded subset of the 512^3 tori domain (about 580 blocks spanning the
+    # whole box, so level 4 has interaction lists), plain bounds (kappa = 1)
+    p = W.block_subset(irregular, 0.08, seed=5, name="tori_subset_512_5lev")
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    st = s.stats()
+    s.close()
+    assert st["n_levels"] == 5 and st["top_product_level"] == 4 and st["compensated_interp"] == 1
+    check(p, plain=True)
 
 
 def test_irregular_512_manufactured(irregular):
-    # exact answer known (Sec. 4.1); kappa ~ 1e3 for this random source
+    # exact answer known (Sec. 4.1).  This random source is badly conditioned:
+    # the FP32 - FP64 difference is bounded relative to max|G * |f||, the size
+    # of the terms summed (the FP64 solve of |f|), not relative to max|u|
     m = W.manufactured(irregular.blocks, 16, 5, 8, seed=7)
     u64 = gpu_solve(m, lgfm.LGF_FP64)
     assert fmm.rel_linf(u64, m.u_exact) < 1e-7
     u32 = gpu_solve(m, lgfm.LGF_FP32)
+    ua = gpu_solve(m, lgfm.LGF_FP64, f=np.abs(m.f))
+    k = float(np.abs(ua).max() / np.abs(u64).max())
     record_error("tori_irregular_512 manufactured", fp64_vs_exact=fmm.rel_linf(u64, m.u_exact),
-                 fp32_vs_exact=fmm.rel_linf(u32, m.u_exact))
-    assert fmm.rel_linf(u32, u64) < 1e-5 * 5e3
+                 fp32_vs_exact=fmm.rel_linf(u32, m.u_exact), fp32_vs_fp64=fmm.rel_linf(u32, u64), kappa=k)
+    assert np.abs(u32 - u64).max() <= TOL32 * np.abs(ua).max()

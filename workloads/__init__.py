@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "full_box_blocks", "gaussian_box", "torus_box", "tori_irregular",
-    "manufactured", "batch_problems", "arrival_stream", "config", "CONFIGS",
+    "manufactured", "batch_problems", "arrival_stream", "config", "CONFIGS", "block_subset", "dipole_box",
 ]
 
 
@@ -156,6 +156,30 @@ def tori_irregular(seed: int = 2, nb: int = 32, n_b: int = 16, n_tori: int = 12,
     keep = np.abs(f).reshape(len(blocks), -1).max(axis=1) > keep_rel * fmax
     return Problem(blocks[keep].copy(), f[keep].copy(), n_b, levels_for(nb), order,
                    f"tori_irregular_{side}")
+
+
+def block_subset(p: Problem, frac: float, seed: int, name: str | None = None) -> Problem:
+    """A seeded random subset of a problem's blocks (each kept with probability
+    frac), with their sources: an irregular, sparser domain spanning the same
+    box, so the tree keeps its depth."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    keep = rng.uniform(size=len(p.blocks)) < frac
+    return Problem(p.blocks[keep].copy(), p.f[keep].copy(), p.n_b, p.n_levels, p.order,
+                   name or f"{p.name}_subset{frac:g}")
+
+
+def dipole_box(nb: int = 8, n_b: int = 8, sigma: float = 4.0, sep: float = 16.0, order: int = 8,
+               n_levels: int | None = None) -> Problem:
+    """A smooth signed source on a full box of nb^3 blocks: two Gaussians of
+    width sigma and opposite sign, sep apart along x about the box centre."""
+    side = nb * n_b
+    blocks = full_box_blocks(nb)
+    x, y, z = _block_points(blocks, n_b)
+    c = (side - 1) / 2.0
+    g = lambda cx: np.exp(-((x - cx) ** 2 + (y - c) ** 2 + (z - c) ** 2) / (2.0 * sigma ** 2))
+    f = g(c - sep / 2.0) - g(c + sep / 2.0)
+    L = levels_for(nb) if n_levels is None else n_levels
+    return Problem(blocks, f, n_b, L, order, f"dipole_{side}_nb{n_b}")
 
 
 def shape_blocks(shape: str, diameter: int, n_b: int) -> np.ndarray:
