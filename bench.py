@@ -419,6 +419,48 @@ def fft_conv_run(torch, lgfm, steps: int, flush, peak_tf: float):
                        "l2": "flushed: 256 MiB write before every timed step"}}
 
 
+def error_sweep_run(torch, lgfm, diameter: int = 128):
+    """The paper's error experiment on the GPU (Sec. 4.1): exact manufactured
+    solutions on a cube, a sphere and a spherical shell of the same diameter,
+    n_max = 10, n_I = n_b + 1 = 11..17; relative L-infinity error of the FP64
+    form, its fitted power of n_I (the paper: -10.7), and the FP32 / FP64
+    rates.  Also the Sec. 2.5 parameter choice for two targets."""
+    out = {"config": {"workload": "manufactured_sweep", "diameter": diameter, "n_max": 10, "n_I": [11, 13, 15, 17]}}
+    for shape in ("box", "sphere", "shell"):
+        rows = []
+        for n_b in (10, 12, 14, 16):
+            blocks = W.shape_blocks(shape, diameter, n_b)
+            L = W.levels_for(int(np.ceil(diameter / n_b)))
+            m = W.manufactured(blocks, n_b, L, 9, seed=11)
+            row = {"n_I": n_b + 1, "points": m.n_points, "levels": L}
+            for prec, name in ((lgfm.LGF_FP64, "fp64"), (lgfm.LGF_FP32, "fp32")):
+                dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+                s = lgfm.Solver(m.blocks, n_b, L, 9, prec)
+                f = torch.from_numpy(m.f).to(dt).cuda()
+                u = torch.empty_like(f)
+                s(f, u)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(3):
+                    s(f, u)
+                b.record()
+                b.synchronize()
+                row[f"{name}_points_per_s"] = 3 * m.n_points / (a.elapsed_time(b) * 1e-3)
+                row[f"{name}_rel_err_vs_exact"] = float(np.abs(u.double().cpu().numpy() - m.u_exact).max()
+                                                        / np.abs(m.u_exact).max())
+                s.close()
+            rows.append(row)
+        slope = float(np.polyfit(np.log([r["n_I"] for r in rows]),
+                                 np.log([r["fp64_rel_err_vs_exact"] for r in rows]), 1)[0])
+        out[shape] = {"rows": rows, "fp64_error_slope_vs_n_I": slope}
+    sel = {}
+    for eps, prec, name in ((1e-5, lgfm.LGF_FP32, "fp32_1e-5"), (1e-9, lgfm.LGF_FP64, "fp64_1e-9"),
+                            (1.25e-12, lgfm.LGF_FP64, "fp64_1.25e-12")):
+        sel[name] = lgfm.lgf_select_interp(eps, prec)
+    out["interp_selection"] = sel
+    return out
+
+
 def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
     """Poisson arrivals (200/s, seed 1) of torus solves with point counts
     log-uniform in 2^12..2^24, admitted under a 120 GB HBM budget, FP32 form
@@ -485,6 +527,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson-arrival serving workload")
     ap.add_argument("--no-irregular", action="store_true", help="skip the 512^3 irregular-domain workload")
     ap.add_argument("--no-fft-conv", action="store_true", help="skip the single-block FFT-convolution workload")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n_max = 10 error sweep")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     args = ap.parse_args()
@@ -715,6 +758,11 @@ def main():
             out["irregular"] = irregular_run(torch, lgfm, max(3, min(50, args.steps // 40)), flush)
         except Exception as exc:
             out["irregular"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if world == 1 and not args.no_sweep:
+        try:
+            out["error_sweep"] = error_sweep_run(torch, lgfm)
+        except Exception as exc:
+            out["error_sweep"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and not args.no_serve:
         try:
             out["serve"] = serve_run(torch, lgfm)

@@ -108,7 +108,10 @@ typedef enum {
  *   block_ijk     host array, n_blocks x 3 int32 block indices (x, y, z);
  *                 unique; copied, the caller keeps ownership
  *   n_blocks      >= 1
- *   n_b           points per block edge: 4, 8 or 16
+ *   n_b           points per block edge, even, 4 <= n_b <= 32 (odd or out of
+ *                 range: LGF_ERR_INVALID_ARG); built: 4, 6, 8, 10, 12, 14, 16
+ *                 (18 .. 32: LGF_ERR_UNSUPPORTED).  The tensor-core
+ *                 interpolation modes need 4, 8 or 16.
  *   n_levels      L >= 1: the leaves are level 1 and the root level is L
  *                 (Sec. 3.1).  Level L must hold intervals that are all near
  *                 one another (at most two per axis, aligned); otherwise
@@ -133,8 +136,9 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  * Tuning options (zero-initialise for the defaults).
  *   fft_size_interval  FFT length per axis S_I at levels >= 1 (Sec. 2.2: any
  *                      S_I >= 2 n_I - 1 gives the same linear convolution).
- *                      0 = default.  Supported: n_b = 4: 10; n_b = 8: 17, 18;
- *                      n_b = 16: 33, 34, 36.  The level-0 length is 2 n_b.
+ *                      0 = default.  Supported: n_b = 4: 10; 6: 16; 8: 17,
+ *                      18; 10: 24; 12: 28; 14: 32; 16: 33, 34, 36.  The
+ *                      level-0 length is 2 n_b.
  *   near_kernel        product kernel of level 0: 0 = default, 1 = fully
  *                      unrolled 4^3-source form, 2 = half-plane pipelined form
  *   interval_kernel    product kernel of levels >= 1 (and of the merged
@@ -182,9 +186,17 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      passes, each line transform split into output classes
  *                      (FP32 plans with n_b 8 or 16); 0 = 1 (the faster form
  *                      as measured)
+ *   level_order        per-level interpolation orders (Sec. 4 notes that the
+ *                      interval sizes and stencils may be tuned per level):
+ *                      level_order[k] is the polynomial degree of the stencil
+ *                      between parent level k + 2 and level k + 1 (Interp
+ *                      from level k + 2, and Reg into it), 1 <= order + 1 <=
+ *                      n_b + 1; 0 = interp_order.  Levels above
+ *                      LGF_LEVEL_ORDERS + 1 use interp_order.
  * All variants compute the same sums (Eq. alg_mult); they differ only in
  * scheduling.
  */
+#define LGF_LEVEL_ORDERS 8
 typedef struct {
     int32_t fft_size_interval;
     int32_t near_kernel;
@@ -193,7 +205,8 @@ typedef struct {
     int32_t separate_level1;
     int32_t free_sms;
     int32_t fft_kernel;
-    int32_t reserved[9];
+    int32_t level_order[LGF_LEVEL_ORDERS];
+    int32_t reserved[1];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */
@@ -357,7 +370,9 @@ lgf_status lgf_solve_host(lgf_plan plan, const void *f_host, void *u_host, void 
 lgf_status lgf_solve_host_pipelined(lgf_plan plan, const void *const *f_host, void *const *u_host,
                                     int32_t n_steps, void *stream);
 
-/* Waits for the plan's last solve and reports any asynchronous error. */
+/* Waits for the plan's last solve (the last one not captured into a graph)
+ * and reports any asynchronous error; other work on the device is not waited
+ * for. */
 lgf_status lgf_plan_sync(lgf_plan plan);
 
 /*
@@ -407,7 +422,11 @@ lgf_status lgf_solve_blocks_noalloc(const void *f_dev, void *u_dev, int64_t n_bl
                                     int32_t precision, void *stream);
 lgf_status lgf_noalloc_max_blocks(int32_t n_b, int32_t precision, int64_t *max_blocks);
 
-/* Frees the plan and its workspace (waits for its device work first). */
+/* Frees the plan and its workspace.  Returns without waiting: the workspace
+ * comes from the stream-ordered allocator and is released once the plan's
+ * last solve has completed, so destroying an idle plan does not stall other
+ * work on the device.  A plan whose solves were captured into a graph must
+ * outlive every launch of that graph (lgf_batch_destroy waits for them). */
 lgf_status lgf_destroy(lgf_plan plan);
 
 /* Message for the calling thread's last failed call ("" if none). */
@@ -424,6 +443,37 @@ const char *lgf_last_error(void);
  */
 lgf_status lgf_green_values(const int32_t *n, int64_t count, double *out);
 lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double *W);
+
+/*
+ * Choice of the interpolation parameters for a target error (Sec. 2.5, the
+ * two-step procedure; host only).
+ *
+ * lgf_lebesgue_constant - Lambda_n of n equally spaced nodes: the maximum
+ *   over their interval of sum_i |l_i(x)| (l_i the Lagrange basis), which
+ *   bounds how much interpolation amplifies perturbations of the nodal
+ *   values (Eq. leb).  1 <= n <= 40.
+ *
+ * lgf_select_interp - Step 1: n_max = the largest node count n with
+ *   Lambda_n^3 eps_p < eps (tensor-product interpolation in 3D; eps_p the
+ *   unit roundoff of the precision, 2^-53 FP64, 2^-24 FP32), n <= 17.
+ *   Step 2: the smallest built block size n_b (4, 6, ..., 16; n_I = n_b + 1
+ *   >= n_max) whose interpolation of the field the method interpolates errs
+ *   by less than eps relative to the field: the LGF of the nearest sources a
+ *   parent interval's interaction list can hold (on the face of the interval
+ *   one interval width away: its corners, edge midpoints and centre),
+ *   interpolated from the parent's nodes (spacing 2) to its children's nodes
+ *   (spacing 1) with the n_max stencil.
+ *     eps          target relative error, 0 < eps < 1
+ *     precision    LGF_FP32 or LGF_FP64 (sets eps_p)
+ *     n_max, n_b   receive the choice (interp_order = n_max - 1)
+ *     lebesgue     receives Lambda_{n_max} (may be NULL)
+ *     interp_err   receives the step-2 error of the chosen n_b (may be NULL)
+ *   LGF_ERR_UNSUPPORTED when no built block size reaches eps; the outputs
+ *   then hold the largest size tried and its error.
+ */
+lgf_status lgf_lebesgue_constant(int32_t n, double *out);
+lgf_status lgf_select_interp(double eps, int32_t precision, int32_t *n_max, int32_t *n_b, double *lebesgue,
+                             double *interp_err);
 
 #ifdef __cplusplus
 }

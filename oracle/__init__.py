@@ -12,6 +12,8 @@ Contents
              1D Bessel-integral form (App. A, Eq. lgf3), FP64
   direct.py  + direct.c: the exact O(N^2) sum u = G * f (Eq. dpoissonsoln), C/OpenMP
   fmm.py     the FLGF method step by step (Sec. 3.1, Steps 0-3), NumPy FP64
+  select.py  the two-step choice of n_max and the interval size for a target
+             error (Sec. 2.5), NumPy FP64
 
 Parity status of each function is stated in its module header.
 """

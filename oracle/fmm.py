@@ -194,14 +194,21 @@ class Spectra:
 # The solve (Steps 1-3)
 
 
-def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra | None = None):
-    """u on every active block, shaped like f (n_blocks, n_b, n_b, n_b) [z, y, x]."""
+def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra | None = None,
+              level_orders: dict | None = None):
+    """u on every active block, shaped like f (n_blocks, n_b, n_b, n_b) [z, y, x].
+
+    level_orders optionally maps a parent level l >= 2 to the interpolation
+    order of the stencil between levels l and l - 1 (Interp from l, Reg into
+    l); other levels use ``order`` (Sec. 4 allows the interval sizes and
+    stencils to differ per level)."""
     blocks = np.asarray(blocks)
     f = np.asarray(f, dtype=np.float64)
     L = int(n_levels)
     n_I = n_b + 1
     S0, S = 2 * n_b, 2 * n_I
-    W = interp_weights(n_b, order + 1)
+    lo = dict(level_orders or {})
+    Wl = {l: interp_weights(n_b, lo.get(l, order) + 1) for l in range(2, L + 1)}
     levels = build_levels(blocks, L)
     sp = Spectra(n_b) if spectra is None else spectra
     bidx = {_key(v): i for i, v in enumerate(blocks)}
@@ -220,7 +227,7 @@ def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra |
                 for c in np.ndindex(2, 2, 2):
                     Q = (2 * P[0] + c[2], 2 * P[1] + c[1], 2 * P[2] + c[0])
                     if Q in ft[l - 1]:
-                        x += reg(W, _child_pos(Q), ft[l - 1][Q])
+                        x += reg(Wl[l], _child_pos(Q), ft[l - 1][Q])
             ft[l][P] = x
         fh[l] = {P: np.fft.rfftn(ft[l][P], s=(S, S, S), axes=(0, 1, 2)) for P in levels[l]}
 
@@ -245,7 +252,7 @@ def fmm_solve(blocks, f, n_b: int, n_levels: int, order: int, spectra: Spectra |
             v = (np.zeros((n_I, n_I, n_I)) if uh[l][P] is None
                  else np.fft.irfftn(uh[l][P], s=(S, S, S), axes=(0, 1, 2))[:n_I, :n_I, :n_I])
             if l < L:
-                v = v + interp(W, _child_pos(P), ut[l + 1][_parent(P)])
+                v = v + interp(Wl[l + 1], _child_pos(P), ut[l + 1][_parent(P)])
             ut[l][P] = v
     u = np.empty_like(f)
     for P in levels[0]:

@@ -67,6 +67,10 @@ _SIGS = {
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_green_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lgf_interp_weights": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "lgf_lebesgue_constant": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "lgf_select_interp": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -126,7 +130,8 @@ class lgf_plan_options(ctypes.Structure):
     _fields_ = [("fft_size_interval", ctypes.c_int32), ("near_kernel", ctypes.c_int32),
                 ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
                 ("separate_level1", ctypes.c_int32), ("free_sms", ctypes.c_int32),
-                ("fft_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("fft_kernel", ctypes.c_int32), ("level_order", ctypes.c_int32 * 8),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -156,17 +161,13 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
                        fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
                        single_stream: int = 0, separate_level1: int = 0, free_sms: int = 0,
-                       fft_kernel: int = 0) -> int:
-    """lgf_plan_create with tuning options (0 = default)."""
+                       fft_kernel: int = 0, level_orders=None) -> int:
+    """lgf_plan_create with tuning options (0 = default); level_orders maps a
+    parent level (2..9) to the interpolation order between it and the level
+    below (the level_order option)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
-    opts = lgf_plan_options()
-    opts.free_sms = free_sms
-    opts.fft_kernel = fft_kernel
-    opts.fft_size_interval = fft_size_interval
-    opts.near_kernel = near_kernel
-    opts.interval_kernel = interval_kernel
-    opts.single_stream = single_stream
-    opts.separate_level1 = separate_level1
+    opts = _options(fft_size_interval, near_kernel, interval_kernel, single_stream, separate_level1, free_sms,
+                    fft_kernel, level_orders)
     out = ctypes.c_void_p()
     _check(library().lgf_plan_create_ex(b.ctypes.data, len(b), n_b, n_levels, interp_order, precision,
                                         interp_mode, ctypes.byref(opts), ctypes.byref(out)),
@@ -175,8 +176,12 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
 
 
 def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0,
-             free_sms=0, fft_kernel=0):
+             free_sms=0, fft_kernel=0, level_orders=None):
     opts = lgf_plan_options()
+    for lvl, order in (level_orders or {}).items():
+        if not 2 <= int(lvl) <= 9:
+            raise ValueError("level_orders keys are parent levels 2..9")
+        opts.level_order[int(lvl) - 2] = int(order)
     opts.free_sms = free_sms
     opts.fft_kernel = fft_kernel
     opts.fft_size_interval = fft_size_interval
@@ -369,7 +374,7 @@ class Solver:
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
                  single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE,
-                 free_sms: int = 0, fft_kernel: int = 0):
+                 free_sms: int = 0, fft_kernel: int = 0, level_orders=None):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
@@ -377,7 +382,7 @@ class Solver:
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
                                        interval_kernel=interval_kernel, single_stream=single_stream,
                                        separate_level1=separate_level1, free_sms=free_sms,
-                                       fft_kernel=fft_kernel)
+                                       fft_kernel=fft_kernel, level_orders=level_orders)
 
     @property
     def dtype(self):
@@ -479,3 +484,24 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+def lgf_lebesgue_constant(n: int) -> float:
+    """Lebesgue constant of n equally spaced nodes (host; see include/lgf.h)."""
+    v = ctypes.c_double()
+    _check(library().lgf_lebesgue_constant(n, ctypes.byref(v)), "lgf_lebesgue_constant")
+    return v.value
+
+
+def lgf_select_interp(eps: float, precision: int) -> dict:
+    """Sec. 2.5's choice of n_max and n_b for a target error (host).  Returns
+    {"n_max", "n_b", "lebesgue", "interp_err", "reached"}; reached is False
+    when no built block size meets eps (the largest one tried is returned)."""
+    nm, nb = ctypes.c_int32(), ctypes.c_int32()
+    lam, err = ctypes.c_double(), ctypes.c_double()
+    st = library().lgf_select_interp(eps, precision, ctypes.byref(nm), ctypes.byref(nb), ctypes.byref(lam),
+                                     ctypes.byref(err))
+    if st not in (LGF_OK, 2):
+        _check(st, "lgf_select_interp")
+    return {"n_max": nm.value, "n_b": nb.value, "lebesgue": lam.value, "interp_err": err.value,
+            "reached": st == LGF_OK}

@@ -50,13 +50,30 @@ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
 }
 
 // ---- twiddle tables ----
-constexpr int kTwSizes[] = {8, 10, 16, 17, 18, 32, 33, 34, 36};
-// offset of size S in the tables: the sizes above, laid end to end
-__host__ __device__ constexpr int tw_offset(int S) {
-    return S == 8 ? 0 : S == 10 ? 8 : S == 16 ? 18 : S == 17 ? 34 : S == 18 ? 51 : S == 32 ? 69
-         : S == 33 ? 101 : S == 34 ? 134 : S == 36 ? 168 : -1;
+// every transform length S of the supported block sizes (level 0: 2 n_b;
+// levels >= 1: the interval lengths)
+constexpr int kTwSizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36};
+constexpr int kTwCount = int(sizeof(kTwSizes) / sizeof(kTwSizes[0]));
+// the i-th size of kTwSizes, usable in device code
+__host__ __device__ constexpr int tw_size(int i) {
+    constexpr int sizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36};
+    return sizes[i];
 }
-constexpr int kTwTotal = 204;
+// offset of size S in the tables: the sizes above, laid end to end (-1 if absent)
+__host__ __device__ constexpr int tw_offset(int S) {
+    int o = 0;
+    for (int i = 0; i < kTwCount; ++i) {
+        if (tw_size(i) == S) return o;
+        o += tw_size(i);
+    }
+    return -1;
+}
+__host__ __device__ constexpr int tw_total() {
+    int o = 0;
+    for (int i = 0; i < kTwCount; ++i) o += tw_size(i);
+    return o;
+}
+constexpr int kTwTotal = tw_total();
 
 // One copy per translation unit (no relocatable device code); each TU fills
 // its own copy through Launch<T>::init_twiddles.
@@ -87,8 +104,10 @@ __device__ __forceinline__ cx<T> twmul(cx<T> a, int j) {
     if (2 * j == TOP) return {-a.x, -a.y};
     if (4 * j == TOP) return {T(-SIGN) * a.y, T(SIGN) * a.x};
     if (4 * j == 3 * TOP) return {T(SIGN) * a.y, T(-SIGN) * a.x};
-    const T c = tw_cos<T>(tw_offset(TOP) + j);
-    const T s = T(SIGN) * tw_sin<T>(tw_offset(TOP) + j);
+    constexpr int kOff = tw_offset(TOP);
+    static_assert(kOff >= 0, "transform length without a twiddle table");
+    const T c = tw_cos<T>(kOff + j);
+    const T s = T(SIGN) * tw_sin<T>(kOff + j);
     return {fma(a.x, c, -a.y * s), fma(a.x, s, a.y * c)};
 }
 
@@ -143,6 +162,8 @@ __device__ __forceinline__ void butterfly(cx<T> (&z)[R]) {
             s[r] = a ? (b ? z[r] + z[R - r] : z[r]) : (b ? z[R - r] : czero<T>());
             d[r] = a ? (b ? z[r] - z[R - r] : z[r]) : (b ? cx<T>{-z[R - r].x, -z[R - r].y} : czero<T>());
         }
+        constexpr int kOff = tw_offset(TOP);
+        static_assert(kOff >= 0, "transform length without a twiddle table");
         const cx<T> z0 = z[0];
         cx<T> out0 = z0;
 #pragma unroll
@@ -155,8 +176,8 @@ __device__ __forceinline__ void butterfly(cx<T> (&z)[R]) {
             for (int r = 1; r <= H; ++r) {
                 if (!(r < RNZ || (R - r) < RNZ)) continue;
                 const int m = (r * k) % R;
-                const T c = tw_cos<T>(tw_offset(TOP) + m * (TOP / R));
-                const T sn = tw_sin<T>(tw_offset(TOP) + m * (TOP / R));
+                const T c = tw_cos<T>(kOff + m * (TOP / R));
+                const T sn = tw_sin<T>(kOff + m * (TOP / R));
                 P.x = fma(s[r].x, c, P.x);
                 P.y = fma(s[r].y, c, P.y);
                 Q.x = fma(d[r].x, sn, Q.x);

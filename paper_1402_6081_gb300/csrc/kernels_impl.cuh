@@ -2084,7 +2084,7 @@ cudaError_t Launch<T>::r2c(int S, int n_in, const T* src, int64_t stride, const 
     LGF_R2C(32, 16) LGF_R2C(33, 16) LGF_R2C(33, 17) LGF_R2C(34, 16) LGF_R2C(34, 17)
     LGF_R2C(36, 16) LGF_R2C(36, 17)
 #undef LGF_R2C
-    return cudaErrorInvalidValue;
+    return LaunchExt<T>::r2c(S, n_in, src, stride, items, n, spec, st);
 }
 
 template <typename T>
@@ -2096,7 +2096,7 @@ cudaError_t Launch<T>::c2r(int S, int n_out, const void* spec, const C2RItem* it
     LGF_C2R(16, 8) LGF_C2R(17, 9) LGF_C2R(18, 9)
     LGF_C2R(32, 16) LGF_C2R(33, 17) LGF_C2R(34, 17) LGF_C2R(36, 17)
 #undef LGF_C2R
-    return cudaErrorInvalidValue;
+    return LaunchExt<T>::c2r(S, n_out, spec, items, n, dst, ds, add, add_n, as, st);
 }
 
 template <typename T, int S>
@@ -2121,7 +2121,16 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
         case 8: return launch_mac_level0<T, 8>(fh, kh, uh, gnbr, n_groups, variant, st);
         case 16: return launch_mac_level0<T, 16>(fh, kh, uh, gnbr, n_groups, variant, st);
         case 32: return launch_mac_level0<T, 32>(fh, kh, uh, gnbr, n_groups, variant, st);
-        default: return cudaErrorInvalidValue;
+        default: {
+            // other lengths: the first form, whose spectrum size is a run-time argument
+            if (n_groups == 0) return cudaSuccess;
+            const int64_t NW = nw_of(S), NWS = nws_of(S);
+            dim3 block(32, 8), grid((n_groups + 7) / 8, unsigned((NW + 31) / 32));
+            dev::k_mac_level0<T><<<grid, block, 0, st>>>(static_cast<const dev::cx<T>*>(fh),
+                                                         static_cast<const dev::cx<T>*>(kh),
+                                                         static_cast<dev::cx<T>*>(uh), gnbr, n_groups, NW, NWS);
+            return cudaGetLastError();
+        }
     }
 }
 
@@ -2199,7 +2208,9 @@ cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, co
     switch (S) {
         LGF_MACI(8) LGF_MACI(10) LGF_MACI(16) LGF_MACI(17) LGF_MACI(18) LGF_MACI(32) LGF_MACI(33) LGF_MACI(34)
         LGF_MACI(36)
-        default: return cudaErrorInvalidValue;
+        default:
+            return LaunchExt<T>::mac_interval(fh, kh, uh, gnbr, order, n_groups, S, variant, include_self, tmap, err,
+                                              st);
     }
 #undef LGF_MACI
 }
@@ -2250,7 +2261,7 @@ cudaError_t Launch<T>::mac_persist(const void* fh, const void* kh, void* uh, con
         switch (S) {
             LGF_MACP(8) LGF_MACP(10) LGF_MACP(16) LGF_MACP(17) LGF_MACP(18) LGF_MACP(32) LGF_MACP(33) LGF_MACP(34)
             LGF_MACP(36)
-            default: return cudaErrorInvalidValue;
+            default: return LaunchExt<T>::mac_persist(fh, kh, uh, pp, S, early, st);
         }
 #undef LGF_MACP
     }
@@ -2296,7 +2307,8 @@ cudaError_t Launch<T>::reg(int n_b, int n_max, const T* child_src, int child_is_
         return launch_reg<T, NI, NM>(child_src, child_is_block, child_index, parent_slot, n_parents, dst, W, comp, st);
     LGF_REG(5, 0) LGF_REG(9, 0) LGF_REG(9, 7) LGF_REG(9, 9) LGF_REG(17, 0) LGF_REG(17, 7) LGF_REG(17, 9)
 #undef LGF_REG
-    return cudaErrorInvalidValue;
+    return LaunchExt<T>::reg(n_b, n_max, child_src, child_is_block, child_index, parent_slot, n_parents, dst, W, comp,
+                             st);
 }
 
 template <typename T>
@@ -2314,7 +2326,7 @@ cudaError_t Launch<T>::interp(int n_b, int n_max, const int* slot, const int* pa
     LGF_INTERP(5, 0) LGF_INTERP(9, 0) LGF_INTERP(9, 7) LGF_INTERP(9, 9) LGF_INTERP(17, 0) LGF_INTERP(17, 7)
     LGF_INTERP(17, 9)
 #undef LGF_INTERP
-    return cudaErrorInvalidValue;
+    return LaunchExt<T>::interp(n_b, n_max, slot, parent, n_items, u, up, W, accumulate, block, comp, st);
 }
 
 }  // namespace lgf

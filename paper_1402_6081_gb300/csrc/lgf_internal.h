@@ -145,6 +145,33 @@ struct Launch {
                               cudaStream_t st);
 };
 
+// The kernels of the block sizes n_b = 6, 10, 12 and 14 (transform lengths
+// 12, 20, 24, 28 at level 0; n_I = 7, 11, 13, 15 at the interval levels),
+// compiled in units of their own (kernels_ext_f32.cu, kernels_ext_f64.cu) so
+// each unit's build stays short.  Launch<T> hands every size it does not
+// have to these; the same arguments and errors (cudaErrorInvalidValue for a
+// size neither has).
+template <typename T>
+struct LaunchExt {
+    static cudaError_t init_twiddles();
+    static cudaError_t r2c(int S, int n_in, const T* src, int64_t src_stride, const R2CItem* items, int n_items,
+                           void* spec, cudaStream_t st);
+    static cudaError_t c2r(int S, int n_out, const void* spec, const C2RItem* items, int n_items, T* dst,
+                           int64_t dst_stride, const T* add, int add_n, int64_t add_stride, cudaStream_t st);
+    static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
+                                    int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
+                                    int* err, cudaStream_t st);
+    static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
+                                   int early, cudaStream_t st);
+    static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block, const int* child_index,
+                           const int* parent_slot, int n_parents, T* dst, const T* W, int comp, cudaStream_t st);
+    static cudaError_t interp(int n_b, int n_max, const int* slot, const int* parent, int n_items, T* u,
+                              const T* up, const T* W, int accumulate, const int* block, int comp,
+                              cudaStream_t st);
+};
+// Transform lengths the persistent products kernel is built for (FP32)
+bool persist_supported(int S);
+
 // Level-0 transforms as persistent kernels, FP32 (kernels_f32.cu): one CTA
 // per SM (grid from cube_fft_grid, which also sets the kernels' shared-memory
 // limit) takes blocks from the counter pair ctr[0..1] (zero between launches)

@@ -46,13 +46,24 @@ static lgf_status cuda_fail(cudaError_t e, const char* where) {
 
 // FFT length along each axis for the interval levels (any S >= 2 n_I - 1 gives
 // the same linear convolution; these are the lengths the kernels are built for).
-int s_interval(int n_b) { return n_b == 4 ? 10 : n_b == 8 ? 18 : 33; }
+int s_interval(int n_b) {
+    switch (n_b) {
+        case 4: return 10;
+        case 6: return 16;
+        case 8: return 18;
+        case 10: return 24;
+        case 12: return 28;
+        case 14: return 32;
+        default: return 33;
+    }
+}
 static bool s_interval_supported(int n_b, int S) {
-    if (n_b == 4) return S == 10;
     if (n_b == 8) return S == 17 || S == 18;
     if (n_b == 16) return S == 33 || S == 34 || S == 36;
-    return false;
+    return S == s_interval(n_b);
 }
+// block sizes with built kernels: the even sizes 4..16
+static bool n_b_supported(int n_b) { return n_b >= 4 && n_b <= 16 && n_b % 2 == 0; }
 
 // ---------------------------------------------------------------------------
 // Interpolation stencil (Sec. 2.5): child c node i sits at parent coordinate
@@ -373,8 +384,13 @@ struct lgf_plan_s {
     std::vector<lgf::DevLevel> lev;
     std::vector<int64_t> pairs, intervals, groups;   // per level, for lgf_plan_get_stats
     void* W = nullptr;                  // device copy (unused by the kernels, kept for tools)
-    std::vector<float> Wf;              // host copies passed by value to Reg / Interp
-    std::vector<double> Wd;
+    // host copies of the 1D stencils passed by value to Reg / Interp, per
+    // parent level l (the stencil between levels l and l - 1), and the
+    // stencil size n_max of each
+    std::vector<std::vector<float>> Wf;
+    std::vector<std::vector<double>> Wd;
+    std::vector<int> nmax_lv;
+    int level_n_max(int l) const { return l < int(nmax_lv.size()) && nmax_lv[size_t(l)] > 0 ? nmax_lv[size_t(l)] : n_max; }
     lgf::C2RItem* out_items = nullptr;
     int n_out = 0;
     std::vector<void*> allocs;
@@ -399,17 +415,30 @@ struct lgf_plan_s {
     // done; join[2]: level-0 products done; join[3]: level-0 inverse FFT done;
     // join[4]: levels >= 2 downward part done
     cudaEvent_t fork = nullptr, join[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // Workspace comes from the stream-ordered allocator on mem_st, so freeing
+    // it waits for the plan's own last solve (done_ev, recorded at the end of
+    // every solve on the caller's stream) instead of the whole device: a
+    // server dropping an idle plan does not stall the requests in flight.
+    cudaStream_t mem_st = nullptr;
+    cudaEvent_t done_ev = nullptr;
 
     ~lgf_plan_s() {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
-        cudaDeviceSynchronize();
-        for (void* p : allocs) cudaFree(p);
-        if (stage_f) cudaFree(stage_f);
-        if (stage_u) cudaFree(stage_u);
-        if (stage_f2) cudaFree(stage_f2);
-        if (stage_u2) cudaFree(stage_u2);
+        // a kernel-spectra table this plan alone still holds is freed with
+        // cudaFree below (lev.clear()): let the plan's last solve finish first
+        bool last_owner = false;
+        for (const auto& D : lev) last_owner = last_owner || (D.kh && D.kh.use_count() == 1);
+        if (last_owner && done_ev) cudaEventSynchronize(done_ev);
+        if (mem_st) {
+            if (done_ev) cudaStreamWaitEvent(mem_st, done_ev, 0);
+            for (void* p : allocs) cudaFreeAsync(p, mem_st);
+            for (void* p : {stage_f, stage_u, stage_f2, stage_u2})
+                if (p) cudaFreeAsync(p, mem_st);
+            cudaStreamDestroy(mem_st);   // returns at once; released when its work is done
+        }
+        if (done_ev) cudaEventDestroy(done_ev);
         for (cudaStream_t c : copy_st)
             if (c) cudaStreamDestroy(c);
         for (cudaEvent_t e : pipe_ev)
@@ -452,15 +481,18 @@ static lgf_status dalloc(lgf_plan_s* P, size_t bytes, void** out, bool zero) {
     if (bytes == 0) return ok();
     if (injected_alloc_failure())
         return fail(LGF_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes: injected failure");
-    cudaError_t e = cudaMalloc(out, bytes);
+    cudaError_t e = cudaMallocAsync(out, bytes, P->mem_st);
+    if (e == cudaSuccess && zero) e = cudaMemsetAsync(*out, 0, bytes, P->mem_st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->mem_st);   // ready for use on any stream
     if (e != cudaSuccess) {
+        if (*out) cudaFreeAsync(*out, P->mem_st);
         *out = nullptr;
+        cudaGetLastError();
         return fail(LGF_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes: " +
                                      cudaGetErrorString(e));
     }
     P->allocs.push_back(*out);
     P->bytes += bytes;
-    if (zero) LGF_CUDA(cudaMemset(*out, 0, bytes));
     return ok();
 }
 
@@ -482,7 +514,10 @@ static std::set<std::pair<int, int>> g_tw_done;
 static lgf_status ensure_twiddles(int device, int prec) {
     std::lock_guard<std::mutex> lock(g_tw_mu);
     if (g_tw_done.count({device, prec})) return ok();
+    // each unit holding transforms has its own copy of the tables
     cudaError_t e = prec == LGF_FP64 ? Launch<double>::init_twiddles() : Launch<float>::init_twiddles();
+    if (e == cudaSuccess)
+        e = prec == LGF_FP64 ? LaunchExt<double>::init_twiddles() : LaunchExt<float>::init_twiddles();
     if (e != cudaSuccess) return cuda_fail(e, "twiddle upload");
     g_tw_done.insert({device, prec});
     return ok();
@@ -533,6 +568,7 @@ static bool shares_sms(const lgf_plan_s* P) {
 }
 static bool uses_persist(const lgf_plan_s* P, int l) {
     if (P->prec != LGF_FP32) return false;
+    if (!persist_supported(l == 0 ? P->S0 : P->SI)) return false;
     if (P->interval_kernel != 0 && P->interval_kernel != 4 && P->interval_kernel != 5) return false;
     if (l == 0 && !P->merged) return false;
     // beside shared-SM level-0 products, levels >= 2 keep the
@@ -968,11 +1004,15 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
         lgf_status s = upload(P, items, &P->out_items);
         if (s != LGF_OK) return s;
     }
-    // interpolation weights in the plan precision
+    // interpolation weights in the plan precision, per parent level
     {
+        P->Wd.assign(size_t(L) + 1, {});
+        P->Wf.assign(size_t(L) + 1, {});
+        for (int l = 0; l <= L; ++l) {
+            P->Wd[size_t(l)] = interp_weights(nb, P->level_n_max(l));
+            P->Wf[size_t(l)].assign(P->Wd[size_t(l)].begin(), P->Wd[size_t(l)].end());
+        }
         std::vector<double> W = interp_weights(nb, P->n_max);
-        P->Wd = W;
-        P->Wf.assign(W.begin(), W.end());
         lgf_status s;
         if (P->prec == LGF_FP64) {
             double* d = nullptr;
@@ -1016,9 +1056,11 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     const int nb = P->n_b, nI = P->n_I;
     const int64_t n3 = int64_t(nI) * nI * nI, b3 = int64_t(nb) * nb * nb;
     auto& lev = P->lev;
-    const T* W = nullptr;
-    if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(P->Wd.data());
-    else W = reinterpret_cast<const T*>(P->Wf.data());
+    // the stencil between parent level l and level l - 1
+    auto Wl = [&](int l) -> const T* {
+        if constexpr (sizeof(T) == 8) return reinterpret_cast<const T*>(P->Wd[size_t(l)].data());
+        else return reinterpret_cast<const T*>(P->Wf[size_t(l)].data());
+    };
     cudaError_t e;
     const int Lm = P->Lmac;
     const bool conc = !P->single_stream;
@@ -1051,10 +1093,14 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     // plain or compensated sums
     const bool tc_mode = P->interp_mode != LGF_INTERP_NATIVE && P->interp_mode != LGF_INTERP_COMPENSATED &&
                          P->interp_mode != LGF_INTERP_PLAIN;
-    // Interp of level l + 1 into the level-l items of D (see Launch::interp);
-    // the CUDA-core form in up to two launches: the items of problems with
-    // compensated sums, then the others
-    auto interp = [&](DevLevel& D, T* out, const T* up, int accumulate, const int* block, cudaStream_t s) {
+    // Interp of level l + 1 into the level-l items of D = lev[l] (see
+    // Launch::interp) with the stencil of parent level l + 1; the CUDA-core
+    // form in up to two launches: the items of problems with compensated
+    // sums, then the others
+    auto interp = [&](int l, T* out, const T* up, int accumulate, const int* block, cudaStream_t s) {
+        DevLevel& D = lev[size_t(l)];
+        const T* W = Wl(l + 1);
+        const int nm = P->level_n_max(l + 1);
         if constexpr (sizeof(T) == 4) {
             if (tc_mode)
                 return interp_tc(P->interp_mode, nb, D.int_slot, D.int_parent, D.n_int, out, up, W, accumulate, block,
@@ -1062,11 +1108,10 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         }
         cudaError_t r = cudaSuccess;
         const int nc = D.n_int_comp;
-        if (nc > 0)
-            r = Lc::interp(nb, P->n_max, D.int_slot, D.int_parent, nc, out, up, W, accumulate, block, 1, s);
+        if (nc > 0) r = Lc::interp(nb, nm, D.int_slot, D.int_parent, nc, out, up, W, accumulate, block, 1, s);
         if (nc > 0 && D.n_int > nc) ++P->launches_last;   // the second launch of this phase
         if (r == cudaSuccess && D.n_int > nc)
-            r = Lc::interp(nb, P->n_max, D.int_slot + nc, D.int_parent + nc, D.n_int - nc, out, up, W, accumulate,
+            r = Lc::interp(nb, nm, D.int_slot + nc, D.int_parent + nc, D.n_int - nc, out, up, W, accumulate,
                            block ? block + nc : nullptr, 0, s);
         return r;
     };
@@ -1077,6 +1122,8 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             const bool from_blocks = l == 2;
             e = timed(P, "reg", s2, [&] {
                 const T* src = from_blocks ? f : static_cast<const T*>(lev[size_t(l) - 1].ft);
+                const T* W = Wl(l);
+                const int nm = P->level_n_max(l);
                 if constexpr (sizeof(T) == 4) {
                     if (tc_mode)
                         return reg_tc(P->interp_mode, nb, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, D.n_reg,
@@ -1085,11 +1132,11 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                 cudaError_t r = cudaSuccess;
                 const int nc = D.n_reg_comp;
                 if (nc > 0)
-                    r = Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, nc,
+                    r = Lc::reg(nb, nm, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, nc,
                                 static_cast<T*>(D.ft), W, 1, s2);
                 if (nc > 0 && D.n_reg > nc) ++P->launches_last;
                 if (r == cudaSuccess && D.n_reg > nc)
-                    r = Lc::reg(nb, P->n_max, src, from_blocks ? 1 : 0, D.reg_child + 8 * size_t(nc),
+                    r = Lc::reg(nb, nm, src, from_blocks ? 1 : 0, D.reg_child + 8 * size_t(nc),
                                 D.reg_parent + nc, D.n_reg - nc, static_cast<T*>(D.ft), W, 0, s2);
                 return r;
             });
@@ -1128,7 +1175,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             }
             if (l < Lm) {
                 e = timed(P, "interp", s2, [&] {
-                    return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[size_t(l) + 1].ut), 1, nullptr,
+                    return interp(l, static_cast<T*>(D.ut), static_cast<const T*>(lev[size_t(l) + 1].ut), 1, nullptr,
                                   s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interpolation");
@@ -1183,7 +1230,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         LGF_CUDA(wait(s2, 3));
         DevLevel& D = lev[1];
         e = timed(P, "interp", s2, [&] {
-            return interp(D, u, static_cast<const T*>(lev[2].ut), 1, D.int_block, s2);
+            return interp(1, u, static_cast<const T*>(lev[2].ut), 1, D.int_block, s2);
         });
         if (e != cudaSuccess) return cuda_fail(e, "interpolation");
         LGF_CUDA(record(4, s2));
@@ -1221,7 +1268,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if (P->merged) {
             DevLevel& D = lev[1];
             e = timed(P, "interp", s2, [&] {
-                return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 0, nullptr, s2);
+                return interp(1, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 0, nullptr, s2);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interpolation");
         }
@@ -1235,7 +1282,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if (!P->merged) {
             DevLevel& D = lev[1];
             e = timed(P, "interp", st, [&] {
-                return interp(D, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 1, nullptr, st);
+                return interp(1, static_cast<T*>(D.ut), static_cast<const T*>(lev[2].ut), 1, nullptr, st);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interpolation");
         }
@@ -1298,8 +1345,11 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     }
     const int64_t n_blocks = offsets[n_problems];
     if (n_blocks > (int64_t(1) << 26)) return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: more than 2^26 blocks");
-    if (n_b != 4 && n_b != 8 && n_b != 16)
-        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: n_b must be 4, 8 or 16");
+    if (n_b < 4 || n_b > 32 || n_b % 2 != 0)
+        return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: n_b must be even, 4 <= n_b <= 32");
+    if (!n_b_supported(n_b))
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: n_b = " + std::to_string(n_b) +
+                                             " is not built (block sizes 4, 6, ..., 16 are)");
     if (interp_order < 0 || interp_order + 1 > n_b + 1)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
@@ -1308,9 +1358,14 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: interp_mode must be 0..5");
     if (interp_mode != LGF_INTERP_NATIVE && interp_mode != LGF_INTERP_PLAIN && precision != LGF_FP32)
         return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: reduced-precision interpolation modes need an FP32 plan");
+    if ((interp_mode == LGF_INTERP_BF16 || interp_mode == LGF_INTERP_FP16 || interp_mode == LGF_INTERP_BF16X3) &&
+        n_b != 4 && n_b != 8 && n_b != 16)
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: tensor-core interpolation modes need n_b 4, 8 or 16");
     auto P = std::make_unique<lgf_plan_s>();
     cudaError_t e = cudaGetDevice(&P->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    LGF_CUDA(cudaStreamCreateWithFlags(&P->mem_st, cudaStreamNonBlocking));
+    LGF_CUDA(cudaEventCreateWithFlags(&P->done_ev, cudaEventDisableTiming));
     P->n_b = n_b;
     P->n_I = n_b + 1;
     P->n_max = interp_order + 1;
@@ -1340,6 +1395,17 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         if (opts->fft_kernel < 0 || opts->fft_kernel > 2)
             return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: fft_kernel must be 0, 1 or 2");
         P->fft_kernel = opts->fft_kernel;
+        // per-level interpolation orders: entry k is the stencil between
+        // parent level k + 2 and level k + 1
+        P->nmax_lv.assign(LGF_LEVEL_ORDERS + 2, 0);
+        for (int k = 0; k < LGF_LEVEL_ORDERS; ++k) {
+            const int o = opts->level_order[k];
+            if (o == 0) continue;
+            if (o < 0 || o + 1 > n_b + 1)
+                return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: level_order[" + std::to_string(k) +
+                                                     "] must be 0 or satisfy 1 <= order + 1 <= n_b + 1");
+            P->nmax_lv[size_t(k) + 2] = o + 1;
+        }
     }
     lgf_status s = ensure_twiddles(P->device, precision);
     if (s != LGF_OK) return s;
@@ -1471,6 +1537,13 @@ lgf_status lgf_solve(lgf_plan plan, const void* f_dev, void* u_dev, void* stream
             ? solve_impl<double>(plan, static_cast<const double*>(f_dev), static_cast<double*>(u_dev), st)
             : solve_impl<float>(plan, static_cast<const float*>(f_dev), static_cast<float*>(u_dev), st);
     nvtxRangePop();
+    if (r == LGF_OK) {
+        // the plan's completion marker (lgf_plan_sync, lgf_destroy); a solve
+        // captured into a graph leaves it to the graph's owner
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LGF_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusNone) LGF_CUDA(cudaEventRecord(plan->done_ev, st));
+    }
     return r;
 }
 
@@ -1494,8 +1567,9 @@ lgf_status lgf_solve_host(lgf_plan plan, const void* f_host, void* u_host, void*
     if (s != LGF_OK) return s;
     const size_t bytes = size_t(plan->n_points) * (plan->prec == LGF_FP64 ? sizeof(double) : sizeof(float));
     if (!plan->stage_f) {
-        cudaError_t e = cudaMalloc(&plan->stage_f, bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->stage_u, bytes);
+        cudaError_t e = cudaMallocAsync(&plan->stage_f, bytes, plan->mem_st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&plan->stage_u, bytes, plan->mem_st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(plan->mem_st);
         if (e != cudaSuccess) return fail(LGF_ERR_OOM, std::string("staging buffers: ") + cudaGetErrorString(e));
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1520,7 +1594,8 @@ lgf_status lgf_solve_host_pipelined(lgf_plan plan, const void* const* f_host, vo
     if (!plan->stage_f2) {
         cudaError_t e = cudaSuccess;
         for (void** p : {&plan->stage_f, &plan->stage_u, &plan->stage_f2, &plan->stage_u2})
-            if (!*p && e == cudaSuccess) e = cudaMalloc(p, bytes);
+            if (!*p && e == cudaSuccess) e = cudaMallocAsync(p, bytes, plan->mem_st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(plan->mem_st);
         if (e != cudaSuccess) return fail(LGF_ERR_OOM, std::string("staging buffers: ") + cudaGetErrorString(e));
         for (cudaStream_t& c : plan->copy_st) LGF_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
         for (cudaEvent_t& e2 : plan->pipe_ev) LGF_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
@@ -1615,7 +1690,7 @@ lgf_status lgf_plan_sync(lgf_plan plan) {
     if (!plan) return fail(LGF_ERR_INVALID_ARG, "lgf_plan_sync: NULL plan");
     lgf_status s = check_device(plan);
     if (s != LGF_OK) return s;
-    LGF_CUDA(cudaDeviceSynchronize());
+    LGF_CUDA(cudaEventSynchronize(plan->done_ev));
     if (plan->err) {
         int flag = 0;
         LGF_CUDA(cudaMemcpy(&flag, plan->err, sizeof(int), cudaMemcpyDeviceToHost));

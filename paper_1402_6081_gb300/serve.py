@@ -11,6 +11,12 @@ Latency is measured from arrival to completion of the copy of u.
 
 The admission logic runs on the host and takes a plan factory and a
 submit/poll pair, so it runs the same with fake plans on a simulated clock.
+A request whose plan must first be made does not hold up the others: with an
+executor the plan is built on a worker thread (host tables, kernel spectra,
+uploads) while the loop keeps admitting and polling, and arrived requests
+behind a waiting one are admitted when an idle plan of their shape exists.
+Dropping an idle plan never waits for the device (the library frees a plan's
+workspace in stream order, after its own last solve).
 """
 from __future__ import annotations
 
@@ -58,31 +64,60 @@ class _Slot:
 
 class PlanPools:
     """Plans per shape under an HBM budget.  make(key) -> (handle, bytes);
-    drop(handle) frees one."""
+    drop(handle) frees one.  With an executor (concurrent.futures), a new plan
+    whose size is known or estimated is made on it: its bytes are reserved
+    against the budget meanwhile and acquire returns None until it is ready."""
 
-    def __init__(self, make, drop, budget_bytes: float):
+    def __init__(self, make, drop, budget_bytes: float, executor=None):
         self.make = make
         self.drop = drop
         self.budget = float(budget_bytes)
         self.used = 0.0
         self.slots: dict = collections.defaultdict(list)
         self.known: dict = {}               # shape -> bytes of its plan
+        self.executor = executor
+        self.making: dict = {}              # shape -> (future, reserved bytes)
 
-    def acquire(self, key, now: float, need_bytes=None):
+    def _collect(self, key, now: float):
+        """The plan made for this shape on the executor, once it is ready."""
+        fut, reserved = self.making[key]
+        if not fut.done():
+            return None
+        del self.making[key]
+        self.used -= reserved
+        handle, nbytes = fut.result()
+        self.known[key] = nbytes
+        s = _Slot(key, handle, nbytes)
+        s.busy = True
+        s.last_used = now
+        self.slots[key].append(s)
+        self.used += nbytes                 # may pass the budget by the estimate's error
+        return s
+
+    def acquire(self, key, now: float, need_bytes=None, allow_new: bool = True):
         """An idle plan of this shape, else a new one if it fits the budget
         (evicting idle plans, least recently used first), else None (wait).
         The size of a new plan is the one measured for this shape before, else
-        need_bytes; with neither, the plan is made and then checked."""
+        need_bytes; with neither, the plan is made and then checked.
+        allow_new=False only takes an idle plan."""
         for s in self.slots[key]:
             if not s.busy:
                 s.busy = True
                 s.last_used = now
                 return s
+        if key in self.making:
+            return self._collect(key, now)
+        if not allow_new:
+            return None
         est = self.known.get(key, need_bytes)
         if est is not None:
             if est > self.budget:
                 raise AdmissionError(f"request {key} needs {est:.3e} B, above the budget {self.budget:.3e} B")
             if not self._make_room(est):
+                return None
+            if self.executor is not None:
+                self.used += est
+                self.making[key] = (self.executor.submit(self.make, key), est)
                 return None
         handle, nbytes = self.make(key)
         self.known[key] = nbytes
@@ -114,6 +149,9 @@ class PlanPools:
         self.drop(slot.handle)
 
     def close(self):
+        for fut, _ in self.making.values():
+            self.drop(fut.result()[0])
+        self.making.clear()
         for ss in self.slots.values():
             for s in ss:
                 self.drop(s.handle)
@@ -127,25 +165,30 @@ def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter
     returns a token; poll(token) -> bool says whether it finished.
     need_bytes(key) (optional) estimates a new plan's bytes before creating it.
     Returns the list of Done records and the rejected request ids."""
-    pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    pending = sorted(requests, key=lambda r: r.arrival)
     inflight = []
     done, rejected = [], []
     t0 = clock()
     while pending or inflight:
         now = clock() - t0
         progressed = False
-        while pending and pending[0].arrival <= now and len(inflight) < max_inflight:
-            r = pending[0]
+        # arrived requests in arrival order; once one has to wait, later ones
+        # only take idle plans of their shape (no new plans ahead of it)
+        i, waiting = 0, False
+        while i < len(pending) and pending[i].arrival <= now and len(inflight) < max_inflight:
+            r = pending[i]
             try:
-                slot = pools.acquire(r.key, now, need_bytes(r.key) if need_bytes else None)
+                slot = pools.acquire(r.key, now, need_bytes(r.key) if need_bytes else None, allow_new=not waiting)
             except AdmissionError:
-                pending.popleft()
+                del pending[i]
                 rejected.append(r.rid)
                 progressed = True
                 continue
             if slot is None:
-                break                       # wait for memory or a plan of this shape
-            pending.popleft()
+                waiting = True              # memory, or its plan is being made
+                i += 1
+                continue
+            del pending[i]
             start = clock() - t0
             inflight.append((r, slot, submit(slot, r), start))
             progressed = True
@@ -161,7 +204,7 @@ def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter
                 still.append(item)
         inflight = still
         if not progressed:
-            if pending and not inflight and pending[0].arrival > now:
+            if pending and not inflight and not pools.making and pending[0].arrival > now:
                 sleep(min(pending[0].arrival - now, 1e-3))
             else:
                 sleep(idle_wait)
@@ -186,7 +229,9 @@ class GpuServer:
     request's own pinned host source (default: the shape's f)."""
 
     def __init__(self, precision: int, problems: dict, budget_bytes: float = 120e9, n_streams: int = 16,
-                 tuned_options=None, source=None, keep_results: bool = False):
+                 tuned_options=None, source=None, keep_results: bool = False, background_plans: bool = True):
+        import concurrent.futures
+
         import torch
 
         import paper_1402_6081_gb300 as lgfm
@@ -204,7 +249,9 @@ class GpuServer:
         self.keep_results = keep_results
         self.results = {}
         self.largest = {}                   # n_b -> (points, bytes) of the largest plan made
-        self.pools = PlanPools(self._make, self._drop, budget_bytes)
+        self.device = torch.cuda.current_device()
+        self.executor = concurrent.futures.ThreadPoolExecutor(1) if background_plans else None
+        self.pools = PlanPools(self._make, self._drop, budget_bytes, executor=self.executor)
 
     def points(self, key) -> int:
         p = self.problems[key]
@@ -220,6 +267,7 @@ class GpuServer:
         return None if big is None else 1.25 * big[1] * self.points(key) / big[0]
 
     def _make(self, key):
+        self.torch.cuda.set_device(self.device)     # also on the plan-making thread
         p = self.problems[key]
         opts = self.tuned.get(key, {})
         s = self.lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, self.precision, **opts)
@@ -233,8 +281,9 @@ class GpuServer:
         return (s, f, u, uh), nbytes
 
     def _drop(self, handle):
+        # only idle plans are dropped (their last solve and copies completed);
+        # the library releases the workspace in stream order, without waiting
         s, f, u, uh = handle
-        self.torch.cuda.synchronize()
         s.close()
 
     def submit(self, slot, req):
@@ -272,3 +321,5 @@ class GpuServer:
     def close(self):
         self.torch.cuda.synchronize()
         self.pools.close()
+        if self.executor is not None:
+            self.executor.shutdown(wait=True)

@@ -77,3 +77,35 @@ def test_error_falls_with_interval_size(shape):
         assert p32 <= 1e-5 * kappa, (n_b, p32, kappa)
         errs.append(e64)
     assert errs[0] > errs[1] > errs[2], errs
+
+
+@pytest.mark.parametrize("shape", ["box", "sphere", "shell"])
+def test_error_trend_at_n_max_10(shape):
+    # The paper's setting (Sec. 4.1): n_max = 10 nodes per point, n_I = n_b + 1
+    # > n_max, where the error should fall like n_I^-10 (measured there:
+    # n_I^-10.7 for n_I = 11..28).  Block sizes 10..16 give n_I = 11..17.
+    errs, n_is = [], []
+    for n_b in (10, 12, 14, 16):
+        blocks = W.shape_blocks(shape, DIAMETER, n_b)
+        L = W.levels_for(int(np.ceil(DIAMETER / n_b)))
+        m = W.manufactured(blocks, n_b, L, 9, seed=11)
+        u64, r64 = _solve(m, lgfm.LGF_FP64)
+        u32, r32 = _solve(m, lgfm.LGF_FP32)
+        ref = fmm.fmm_solve(m.blocks, m.f, n_b, L, 9)
+        kappa = max(1.0, float(np.abs(fmm.fmm_solve(m.blocks, np.abs(m.f), n_b, L, 9)).max()
+                               / np.abs(ref).max()))
+        e64, e_orc = fmm.rel_linf(u64, m.u_exact), fmm.rel_linf(ref, m.u_exact)
+        p64, p32 = fmm.rel_linf(u64, ref), fmm.rel_linf(u32, ref)
+        record_error(f"sweep10_{shape}_nI{n_b + 1}", fp64_vs_exact=e64, oracle_vs_exact=e_orc, fp64_vs_oracle=p64,
+                     fp32_vs_oracle=p32, kappa=kappa, points=m.n_points, fp64_points_per_s=r64,
+                     fp32_points_per_s=r32)
+        print(f"n_max 10 {shape} n_I {n_b + 1}: fp64 err {e64:.3e} (oracle {e_orc:.3e}) vs oracle {p64:.2e}/"
+              f"{p32:.2e} kappa {kappa:.0f}")
+        assert p64 <= 1e-12 * kappa and p32 <= 1e-5 * kappa, (n_b, p64, p32, kappa)
+        errs.append(e64)
+        n_is.append(n_b + 1)
+    slope = float(np.polyfit(np.log(n_is), np.log(errs), 1)[0])
+    record_error(f"sweep10_{shape}_slope", slope=slope)
+    print(f"n_max 10 {shape}: error ~ n_I^{slope:.2f}")
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert -13.0 < slope < -9.0, slope

@@ -128,3 +128,53 @@ def test_sizes_learned_from_the_first_plan_of_a_shape():
     assert len(done) == 300 and not rejected
     assert pools.known == {"a": 30, "b": 50, "c": 20}
     assert pools.used <= 400
+
+
+def test_plan_made_in_the_background_does_not_block_others():
+    # a shape whose plan takes long to make: with an executor the loop keeps
+    # serving the requests of a shape that has an idle plan meanwhile
+    import concurrent.futures
+    import threading
+    import time as _time
+
+    sim = Sim({"fast": 10, "slow": 10}, {"fast": 1e-3, "slow": 1e-3})
+    lock = threading.Lock()
+    release = threading.Event()
+
+    def make(key):
+        if key == "slow":
+            release.wait(5.0)            # held until the fast requests went through
+        with lock:
+            return sim.make(key)
+
+    def drop(h):
+        with lock:
+            sim.drop(h)
+
+    ex = concurrent.futures.ThreadPoolExecutor(1)
+    pools = PlanPools(make, drop, budget_bytes=100, executor=ex)
+    warm = pools.acquire("fast", 0.0, need_bytes=10)
+    assert warm is None                  # made on the executor
+    while pools.acquire("fast", 0.0) is None:
+        _time.sleep(1e-3)
+    pools.release(pools.slots["fast"][0], 0.0)
+    reqs = [Request(0, 0.0, "slow", 1)] + [Request(i, 1e-3 * i, "fast", 1) for i in range(1, 11)]
+    n_fast_done = []
+
+    def poll(tok):
+        done = sim.poll(tok)
+        if done:
+            n_fast_done.append(1)
+            if len(n_fast_done) >= 10:
+                release.set()
+        return done
+
+    done, rejected = run_stream(reqs, pools, sim.submit, poll, clock=sim.clock, sleep=sim.sleep,
+                                need_bytes=lambda k: sim.sizes[k])
+    pools.close()
+    ex.shutdown()
+    assert not rejected and len(done) == 11
+    d = {x.rid: x for x in done}
+    # every fast request finished before the slow one could start
+    assert all(d[i].finish <= d[0].start for i in range(1, 11))
+    assert sim.made == 2
