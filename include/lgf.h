@@ -193,6 +193,21 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      from level k + 2, and Reg into it), 1 <= order + 1 <=
  *                      n_b + 1; 0 = interp_order.  Levels above
  *                      LGF_LEVEL_ORDERS + 1 use interp_order.
+ *   symmetric_spectra  1: the levels whose products run one CTA per
+ *                      frequency chunk (not the persistent form) store only
+ *                      the 40 representatives of the 343 kernel offsets under
+ *                      the reflections and axis exchanges that leave G
+ *                      unchanged (Sec. 3.2: a reflected offset's spectrum is
+ *                      the representative's at reflected frequencies; the
+ *                      kernel vector is centred on index 0, so no twiddle is
+ *                      needed), 4.3x fewer rows than the 172-row half table;
+ *                      the products gather each offset's coefficients from
+ *                      its representative.  0 / 2: the half tables.
+ *   mac_groups_per_cta the interaction-list chunk of the one-CTA-per-chunk
+ *                      products: sibling groups (each with its list of
+ *                      neighbour groups) a CTA takes for one frequency chunk,
+ *                      rounded up to whole warps; 0 = chosen from the level's
+ *                      size (about four waves of CTAs)
  * All variants compute the same sums (Eq. alg_mult); they differ only in
  * scheduling.
  */
@@ -206,7 +221,9 @@ typedef struct {
     int32_t free_sms;
     int32_t fft_kernel;
     int32_t level_order[LGF_LEVEL_ORDERS];
-    int32_t reserved[1];
+    int32_t symmetric_spectra;
+    int32_t mac_groups_per_cta;
+    int32_t reserved[7];
 } lgf_plan_options;
 
 /* lgf_plan_create with options (NULL = defaults). */

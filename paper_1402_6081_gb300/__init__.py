@@ -131,7 +131,8 @@ class lgf_plan_options(ctypes.Structure):
                 ("interval_kernel", ctypes.c_int32), ("single_stream", ctypes.c_int32),
                 ("separate_level1", ctypes.c_int32), ("free_sms", ctypes.c_int32),
                 ("fft_kernel", ctypes.c_int32), ("level_order", ctypes.c_int32 * 8),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("symmetric_spectra", ctypes.c_int32), ("mac_groups_per_cta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class lgf_plan_stats(ctypes.Structure):
@@ -161,13 +162,14 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
                        precision: int = LGF_FP32, interp_mode: int = LGF_INTERP_NATIVE,
                        fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
                        single_stream: int = 0, separate_level1: int = 0, free_sms: int = 0,
-                       fft_kernel: int = 0, level_orders=None) -> int:
+                       fft_kernel: int = 0, level_orders=None, symmetric_spectra: int = 0,
+                       mac_groups_per_cta: int = 0) -> int:
     """lgf_plan_create with tuning options (0 = default); level_orders maps a
     parent level (2..9) to the interpolation order between it and the level
     below (the level_order option)."""
     b = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32).reshape(-1, 3))
     opts = _options(fft_size_interval, near_kernel, interval_kernel, single_stream, separate_level1, free_sms,
-                    fft_kernel, level_orders)
+                    fft_kernel, level_orders, symmetric_spectra, mac_groups_per_cta)
     out = ctypes.c_void_p()
     _check(library().lgf_plan_create_ex(b.ctypes.data, len(b), n_b, n_levels, interp_order, precision,
                                         interp_mode, ctypes.byref(opts), ctypes.byref(out)),
@@ -176,8 +178,10 @@ def lgf_plan_create_ex(blocks, n_b: int, n_levels: int, interp_order: int,
 
 
 def _options(fft_size_interval=0, near_kernel=0, interval_kernel=0, single_stream=0, separate_level1=0,
-             free_sms=0, fft_kernel=0, level_orders=None):
+             free_sms=0, fft_kernel=0, level_orders=None, symmetric_spectra=0, mac_groups_per_cta=0):
     opts = lgf_plan_options()
+    opts.symmetric_spectra = symmetric_spectra
+    opts.mac_groups_per_cta = mac_groups_per_cta
     for lvl, order in (level_orders or {}).items():
         if not 2 <= int(lvl) <= 9:
             raise ValueError("level_orders keys are parent levels 2..9")
@@ -374,7 +378,8 @@ class Solver:
     def __init__(self, blocks, n_b: int, n_levels: int, interp_order: int, precision: int = LGF_FP32,
                  fft_size_interval: int = 0, near_kernel: int = 0, interval_kernel: int = 0,
                  single_stream: int = 0, separate_level1: int = 0, interp_mode: int = LGF_INTERP_NATIVE,
-                 free_sms: int = 0, fft_kernel: int = 0, level_orders=None):
+                 free_sms: int = 0, fft_kernel: int = 0, level_orders=None, symmetric_spectra: int = 0,
+                 mac_groups_per_cta: int = 0):
         self.n_b = n_b
         self.precision = precision
         self.n_blocks = int(np.asarray(blocks).reshape(-1, 3).shape[0])
@@ -382,7 +387,8 @@ class Solver:
                                        fft_size_interval=fft_size_interval, near_kernel=near_kernel,
                                        interval_kernel=interval_kernel, single_stream=single_stream,
                                        separate_level1=separate_level1, free_sms=free_sms,
-                                       fft_kernel=fft_kernel, level_orders=level_orders)
+                                       fft_kernel=fft_kernel, level_orders=level_orders,
+                                       symmetric_spectra=symmetric_spectra, mac_groups_per_cta=mac_groups_per_cta)
 
     @property
     def dtype(self):

@@ -1,11 +1,17 @@
 """Autotuner for the solver's scheduling options.
 
-For one problem shape it times every candidate option set on the current GPU
-(CUDA events, a few warm solves each) and keeps the fastest.  The choices only
+For one problem shape it times candidate option sets on the current GPU (CUDA
+events, a few warm solves each) and keeps the fastest.  The choices only
 change scheduling, never the method: the interval FFT length S_I (any S_I >=
-2 n_I - 1 is exact) and the interaction-kernel variant.  Results are cached
-per (GPU name, n_b, precision, levels, block-count bucket) in a JSON file
-($LGF_TUNE_CACHE, default ~/.cache/paper_1402_6081_gb300/autotune.json).
+2 n_I - 1 is exact), the interaction-kernel form, the SMs left to the levels
+>= 2 chain, the level-0 FFT form (the FFT tile: one block per CTA, or a
+persistent CTA per SM streaming blocks), the kernel tables (half tables or
+reflection-reduced ones) and the interaction-list chunk (sibling groups per
+CTA of the one-CTA-per-chunk products).  The search is coordinate-wise: from
+the library's defaults, each dimension in turn is set to each of its values
+with the others held at the best so far.  Results are cached per (GPU name,
+n_b, precision, levels, block-count bucket) in a JSON file ($LGF_TUNE_CACHE,
+default ~/.cache/paper_1402_6081_gb300/autotune.json).
 """
 from __future__ import annotations
 
@@ -21,16 +27,34 @@ from . import LGF_FP32
 
 _LOCK = threading.Lock()
 
-# interval_kernel 0 = the library's choice (persistent form where a level has
-# enough groups), 1 = one CTA per frequency chunk, 3 = paired groups;
-# free_sms: SMs left to levels >= 2 beside the persistent products (-1: none)
-CANDIDATES = {
-    4: [{"fft_size_interval": 10, "interval_kernel": k} for k in (0, 1)],
-    8: ([{"fft_size_interval": s, "interval_kernel": k} for s in (17, 18) for k in (0, 1, 3)]
-        + [{"fft_size_interval": 17, "interval_kernel": 0, "free_sms": f} for f in (-1, 8, 32)]),
-    16: ([{"fft_size_interval": s, "interval_kernel": k} for s in (33, 34, 36) for k in (0, 1)]
-         + [{"fft_size_interval": 33, "interval_kernel": 0, "free_sms": f} for f in (-1, 8, 32)]),
+# Values per dimension (0 = the library's choice).  interval_kernel: 1 = one
+# CTA per frequency chunk, 3 = paired groups; free_sms: SMs left to levels >= 2
+# beside the persistent products (-1: none); fft_kernel 2: persistent level-0
+# transforms (FP32, n_b 8 or 16); mac_groups_per_cta: the interaction-list chunk
+DIMENSIONS = {
+    "fft_size_interval": {4: [0], 8: [0, 17], 16: [0, 34, 36]},
+    "interval_kernel": [0, 1, 3],
+    "free_sms": [0, -1, 8, 16, 32],
+    "fft_kernel": [0, 2],
+    "symmetric_spectra": [0, 1],
+    "mac_groups_per_cta": [0, 8, 32, 128],
 }
+
+
+def candidates(n_b: int, precision: int):
+    """The dimensions searched for this block size and precision, in order."""
+    dims = []
+    for name, vals in DIMENSIONS.items():
+        v = vals.get(n_b, [0]) if isinstance(vals, dict) else list(vals)
+        if precision != LGF_FP32 and name in ("fft_kernel", "free_sms"):
+            v = [0]
+        if precision != LGF_FP32 and name == "interval_kernel":
+            v = [0, 1]
+        if name == "fft_kernel" and n_b not in (8, 16):
+            v = [0]
+        if len(v) > 1:
+            dims.append((name, v))
+    return dims
 
 
 def cache_path() -> pathlib.Path:
@@ -111,18 +135,32 @@ def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = 
             hit = _load().get(key)
         if hit is not None:
             return dict(hit["options"])
-    cands = CANDIDATES.get(n_b, [{}])
-    if precision != LGF_FP32:
-        cands = [c for c in cands if c.get("interval_kernel", 1) in (0, 1)]
     timings = []
-    for c in cands:
+
+    def measure(opts):
         try:
-            timings.append((time_options(blocks_list, n_b, levels_list, order, precision, c, reps=reps), c))
+            ms = time_options(blocks_list, n_b, levels_list, order, precision, opts, reps=reps)
         except Exception:
-            continue
-    if not timings:
+            return None
+        timings.append((ms, dict(opts)))
+        return ms
+
+    best = {}
+    best_ms = measure(best)
+    if best_ms is None:
         return {}
-    best_ms, best = min(timings, key=lambda t: t[0])
+    for name, values in candidates(n_b, precision):
+        for v in values:
+            if v == best.get(name, 0):
+                continue
+            trial = dict(best)
+            if v == 0:
+                trial.pop(name, None)
+            else:
+                trial[name] = v
+            ms = measure(trial)
+            if ms is not None and ms < best_ms:
+                best_ms, best = ms, trial
     if use_cache:
         with _LOCK:
             d = _load()

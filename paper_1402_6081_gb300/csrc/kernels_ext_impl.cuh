@@ -61,14 +61,14 @@ cudaError_t LaunchExt<T>::c2r(int S, int n_out, const void* spec, const C2RItem*
 template <typename T>
 cudaError_t LaunchExt<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                        int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
-                                       int* err, cudaStream_t st) {
+                                       int* err, cudaStream_t st, int oct, int gpc) {
     // the two-frequency and paired variants stay with the sizes 4, 8, 16
     const int v = variant == 2 || variant == 3 ? 1 : variant;
     switch (S) {
-        case 12: return launch_mac_interval<T, 12>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st);
-        case 20: return launch_mac_interval<T, 20>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st);
-        case 24: return launch_mac_interval<T, 24>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st);
-        case 28: return launch_mac_interval<T, 28>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st);
+        case 12: return launch_mac_interval<T, 12>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st, oct, gpc);
+        case 20: return launch_mac_interval<T, 20>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st, oct, gpc);
+        case 24: return launch_mac_interval<T, 24>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st, oct, gpc);
+        case 28: return launch_mac_interval<T, 28>(fh, kh, uh, gnbr, order, n_groups, v, include_self, tmap, err, st, oct, gpc);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "fft_device.cuh"
@@ -368,6 +369,68 @@ __device__ __forceinline__ void mirror_rows(cx<T>* sk, int tid, int nthreads) {
     }
 }
 
+// Tables reduced by the reflections of G (Sec. 3.2, last paragraph): G is even
+// in each coordinate and symmetric in its arguments, so the kernel vector of
+// offset d = (dx, dy, dz) is that of its representative r = (|dx|,
+// min(|dy|, |dz|), max(|dy|, |dz|)) with the axes reflected (m_a -> s_a m_a,
+// s_a the sign of d_a) and, when |dy| > |dz|, y and z exchanged.  The vector
+// sits symmetrically about index 0 of the circular grid, so its spectrum is
+// the representative's at the reflected and exchanged frequency, with no
+// twiddle factor: khat_d(k) = khat_r(P S k), S = diag(s), P the y-z exchange.
+// A reflected x frequency leaves the stored half (kx in [0, S/2]); there
+// khat_r(-kx, ky', kz') = conj(khat_r(kx, -ky', -kz')) (real kernel vector).
+// The 40 representatives (|dx| 0..3 times the 10 pairs a <= b of 0..3) are
+// the rows of the reduced table, row 10 |dx| + b (b + 1) / 2 + a, instead of
+// the 172 stored rows of the half table.
+constexpr int kOctRows = 40;
+__host__ __device__ constexpr int oct_row(int ax, int a, int b) { return 10 * ax + b * (b + 1) / 2 + a; }
+
+// The coefficient rows 171..342 of frequencies w0 .. w0+31 gathered from the
+// reduced table (the caller mirrors rows 0..170 by conjugation, as for the
+// half table).  Each thread keeps one lane (one frequency) for every row it
+// fills, so the frequency's reflected indices are computed once, and issues
+// its gathers in batches of eight before storing them.
+template <typename T, int S, int NT>
+__device__ __forceinline__ void stage_coefficients_oct(cx<T>* __restrict__ sk, const cx<T>* __restrict__ kr,
+                                                       int64_t w0, int tid) {
+    constexpr int NX = S / 2 + 1;
+    constexpr int64_t NW = int64_t(NX) * S * S, NWS = (NW + 31) / 32 * 32;
+    constexpr int kRowsPerPass = NT / 32, kBatch = 8;
+    static_assert(NT % 32 == 0, "whole warps");
+    const int lane = tid & 31;
+    const int64_t w = w0 + lane;
+    const bool live = w < NW;
+    const int wi = live ? int(w) : 0;
+    const int kx = wi % NX, ky = (wi / NX) % S, kz = wi / (NX * S);
+    const int nky = ky == 0 ? 0 : S - ky, nkz = kz == 0 ? 0 : S - kz;
+    for (int base = kSymFirst + (tid >> 5); base < 343; base += kBatch * kRowsPerPass) {
+        cx<T> v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int row = base + j * kRowsPerPass;
+            v[j] = czero<T>();
+            if (row < 343 && live) {
+                const int dx = row % 7 - 3, dy = (row / 7) % 7 - 3, dz = row / 49 - 3;
+                const int ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+                const bool xneg = dx < 0, swap = ay > az;
+                // signs applied to (ky, kz); a reflected x frequency folds back
+                // with the y and z signs flipped and the value conjugated
+                const bool fy = (dy < 0) != xneg, fz = (dz < 0) != xneg;
+                const int ky1 = fy ? nky : ky, kz1 = fz ? nkz : kz;
+                const int kyy = swap ? kz1 : ky1, kzz = swap ? ky1 : kz1;
+                const int r = oct_row(xneg ? -dx : dx, swap ? az : ay, swap ? ay : az);
+                v[j] = ldg_cx(kr + int64_t(r) * NWS + (int64_t(kzz) * S + kyy) * NX + kx);
+                if (xneg) v[j] = conjx(v[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int row = base + j * kRowsPerPass;
+            if (row < 343) sk[row * 32 + lane] = v[j];
+        }
+    }
+}
+
 // Packed form of the 8 x 8 sibling products (fma.rn.f32x2: two FP32 FMAs per
 // instruction).  With F = Fx + i Fy and K = Kx + i Ky, A accumulates
 // (Fx Kx, Fx Ky) and B accumulates (Fy Kx, Fy Ky), both against K as stored;
@@ -546,7 +609,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? 2 : 1) k_mac_inte
                                                                    const int* __restrict__ order, int n_groups,
                                                                    int groups_per_cta, int include_self,
                                                                    const __grid_constant__ CUtensorMap tmap,
-                                                                   int use_tma, int* __restrict__ err) {
+                                                                   int use_tma, int* __restrict__ err, int oct) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     constexpr int64_t NWS = (NW + 31) / 32 * 32;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -554,7 +617,14 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? 2 : 1) k_mac_inte
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(cx<T>) * 343 * 32);
     const int64_t w0 = int64_t(blockIdx.y) * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    if (use_tma) {
+    if (oct) {
+        // the reflection-reduced table: the stored half's rows gathered by
+        // their frequency maps, the other half by conjugation
+        stage_coefficients_oct<T, S, 32 * WARPS>(sk, kh, w0, tid);
+        __syncthreads();
+        mirror_rows(sk, tid, 32 * WARPS);
+        __syncthreads();
+    } else if (use_tma) {
         // the chunk's stored rows as one tensor box (x in reals: 2 per complex)
         if (tid == 0) {
             mbar_init(bar, 1);
@@ -2137,7 +2207,7 @@ cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, cons
 template <typename T, int S>
 static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                        int n_groups, int variant, int include_self, const CUtensorMap* tmap, int* err,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, int oct = 0, int gpc = 0) {
     constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
     const auto* f = static_cast<const dev::cx<T>*>(fh);
     const auto* k = static_cast<const dev::cx<T>*>(kh);
@@ -2145,12 +2215,16 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
     // groups per CTA: at least one per warp, and enough CTAs for ~4 waves;
     // several groups per warp even out uneven neighbour counts
     auto groups_per_cta = [&](int warps, int per_sm, int64_t nchunks) {
+        // a caller's choice (the interaction-list chunk of the autotuner):
+        // whole warps' worth of groups
+        if (gpc > 0) return std::max(warps, (gpc + warps - 1) / warps * warps);
         int per = warps;
         while (per < n_groups && int64_t((n_groups + 2 * per - 1) / (2 * per)) * nchunks >= 4 * per_sm * 152)
             per *= 2;
         return per;
     };
     if (include_self && variant == 2) variant = 1;
+    if (oct && (variant == 2 || variant == 3)) variant = 1;   // those stage the half table themselves
     if (variant == 3 && sizeof(T) == 4) {
         const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
         auto kern = dev::k_mac_interval_pair<T, S>;
@@ -2194,23 +2268,25 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (tmap) map = *tmap;
-    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self, map, tmap ? 1 : 0, err);
+    kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self, map, tmap && !oct ? 1 : 0, err,
+                                    oct);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
-                                    int* err, cudaStream_t st) {
+                                    int* err, cudaStream_t st, int oct, int gpc) {
 #define LGF_MACI(SS)                                                                                            \
     case SS:                                                                                                    \
-        return launch_mac_interval<T, SS>(fh, kh, uh, gnbr, order, n_groups, variant, include_self, tmap, err, st);
+        return launch_mac_interval<T, SS>(fh, kh, uh, gnbr, order, n_groups, variant, include_self, tmap, err, st, \
+                                          oct, gpc);
     switch (S) {
         LGF_MACI(8) LGF_MACI(10) LGF_MACI(16) LGF_MACI(17) LGF_MACI(18) LGF_MACI(32) LGF_MACI(33) LGF_MACI(34)
         LGF_MACI(36)
         default:
             return LaunchExt<T>::mac_interval(fh, kh, uh, gnbr, order, n_groups, S, variant, include_self, tmap, err,
-                                              st);
+                                              st, oct, gpc);
     }
 #undef LGF_MACI
 }

@@ -124,9 +124,12 @@ struct Launch {
     // include_self: the group's own block is a source (merged levels 0 and 1)
     // tmap: the kernel table as a 2D tensor for TMA loads of the coefficient
     // chunk (nullptr: plain loads); err: device flag for a wait that ran out
+    // oct: kh is the 40-row reflection-reduced table (Sec. 3.2), gathered per
+    // frequency instead of read as the half table; gpc: sibling groups per
+    // CTA (the interaction-list chunk; 0 = from the level's size)
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
-                                    int* err, cudaStream_t st);
+                                    int* err, cudaStream_t st, int oct = 0, int gpc = 0);
     // The same products as mac_interval from a persistent kernel (one CTA per
     // SM) that stages the coefficient chunks with bulk copies; FP32 only.
     // early: launched with programmatic serialization behind the forward FFT
@@ -160,7 +163,7 @@ struct LaunchExt {
                            int64_t dst_stride, const T* add, int add_n, int64_t add_stride, cudaStream_t st);
     static cudaError_t mac_interval(const void* fh, const void* kh, void* uh, const int* gnbr, const int* order,
                                     int n_groups, int S, int variant, int include_self, const CUtensorMap* tmap,
-                                    int* err, cudaStream_t st);
+                                    int* err, cudaStream_t st, int oct, int gpc);
     static cudaError_t mac_persist(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S,
                                    int early, cudaStream_t st);
     static cudaError_t reg(int n_b, int n_max, const T* child_src, int child_is_block, const int* child_index,

@@ -123,9 +123,10 @@ struct SpecEntry {
 };
 
 struct SpecKey {
-    int device, n_b, S, h, near, prec;
+    int device, n_b, S, h, near, prec, oct;
     bool operator<(const SpecKey& o) const {
-        return std::tie(device, n_b, S, h, near, prec) < std::tie(o.device, o.n_b, o.S, o.h, o.near, o.prec);
+        return std::tie(device, n_b, S, h, near, prec, oct) <
+               std::tie(o.device, o.n_b, o.S, o.h, o.near, o.prec, o.oct);
     }
 };
 
@@ -216,9 +217,13 @@ static std::map<SpecKey, std::weak_ptr<SpecEntry>> g_spec_cache;
 // filled: level 0 near field and level-1 interaction list on the block grid)
 enum SpecKind { kNear = 0, kInterval = 1, kBlock = 2 };
 
+// oct (343-offset kinds only): store the 40 representatives of the offsets
+// under the reflections of G instead of the 172-row half table (the products
+// kernel maps each offset's frequencies onto its representative's)
 static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int prec,
-                              std::shared_ptr<SpecEntry>& out) {
-    const SpecKey key{device, n_b, S, h, kind, prec};
+                              std::shared_ptr<SpecEntry>& out, int oct = 0) {
+    if (kind == kNear) oct = 0;
+    const SpecKey key{device, n_b, S, h, kind, prec, oct};
     std::lock_guard<std::mutex> lock(g_spec_mu);
     auto it = g_spec_cache.find(key);
     if (it != g_spec_cache.end()) {
@@ -236,14 +241,29 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
     // conjugate: the 343-offset tables keep only the rows id >= 171 (d = 0 and
     // the offsets after it in x-fastest order); row id < 171 is the conjugate
     // of row 342 - id.  The 27-offset table is kept whole.
-    const int nd = near ? 27 : 172;
+    const int nd = near ? 27 : oct ? 40 : 172;
     const int first = near ? 0 : 171;
     const int64_t NW = nw_of(S), NWS = nws_of(S);
     std::vector<std::complex<double>> all(size_t(nd) * NWS, 0.0);
+    // offset of a stored row: the 27- or 343-offset id, or the representative
+    // (|dx|, a, b), a <= b, of the reduced table (row 10 |dx| + b (b + 1) / 2 + a)
+    auto offset_of = [&](int row, int d[3]) {
+        if (oct) {
+            const int ax = row / 10, p = row % 10, b = p >= 6 ? 3 : p >= 3 ? 2 : p >= 1 ? 1 : 0;
+            d[0] = ax;
+            d[1] = p - b * (b + 1) / 2;
+            d[2] = b;
+            return;
+        }
+        const int id = first + row, r = near ? 3 : 7, o = near ? 1 : 3;
+        d[0] = id % r - o;
+        d[1] = (id / r) % r - o;
+        d[2] = id / (r * r) - o;
+    };
     std::vector<int> todo;
     for (int row = 0; row < nd; ++row) {
-        const int id = first + row, r = near ? 3 : 7, o = near ? 1 : 3;
-        const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
+        int d[3];
+        offset_of(row, d);
         const bool is_near = std::abs(d[0]) <= 1 && std::abs(d[1]) <= 1 && std::abs(d[2]) <= 1;
         if (kind != kInterval || !is_near) todo.push_back(row);
     }
@@ -252,9 +272,9 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
     for (unsigned w = 0; w < nthr; ++w)
         th.emplace_back([&, w] {
             for (size_t t = w; t < todo.size(); t += nthr) {
-                const int row = todo[t], id = first + row;
-                const int r = near ? 3 : 7, o = near ? 1 : 3;
-                const int d[3] = {id % r - o, (id / r) % r - o, id / (r * r) - o};
+                const int row = todo[t];
+                int d[3];
+                offset_of(row, d);
                 kernel_spectrum(n_b, n, h, S, d, tab->data(), V, &all[size_t(row) * NWS]);
             }
         });
@@ -280,7 +300,7 @@ static lgf_status get_spectra(int device, int n_b, int S, int h, int kind, int p
         ce = cudaMemcpy(e->ptr, f.data(), e->bytes, cudaMemcpyHostToDevice);
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "spectra upload");
-    e->has_tmap = !near && encode_table_map(*e, nd, NWS, prec);
+    e->has_tmap = !near && !oct && encode_table_map(*e, nd, NWS, prec);
     g_spec_cache[key] = e;
     out = e;
     return ok();
@@ -346,6 +366,7 @@ struct DevLevel {
     int* int_block = nullptr;       // level 1: the block of each item (output into the blocks)
     int n_int = 0;
     std::shared_ptr<SpecEntry> kh;
+    bool oct = false;               // kh holds the 40 reflection representatives
     PersistPlan pp;                 // work lists and CTA ranges of the persistent products (FP32)
 };
 
@@ -372,6 +393,8 @@ struct lgf_plan_s {
     // form (FP32); grids of the persistent form and its block counters
     // ([0..1] forward, [2..3] inverse)
     int fft_kernel = 0;
+    int symmetric_spectra = 0;          // option: 1 = reflection-reduced interval tables
+    int mac_gpc = 0;                    // option: sibling groups per CTA of the one-CTA-per-chunk products
     int cube_grid[2] = {0, 0};
     int* fft_ctr = nullptr;
     // the forward transform's input map, re-encoded when the input moves
@@ -923,7 +946,10 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             if ((s = upload(P, items, &D.r2c)) != LGF_OK) return s;
             const int h = l == 0 ? 1 : (1 << (l - 1));
             const int kind = l == 0 ? (P->merged ? kBlock : kNear) : kInterval;
-            if ((s = get_spectra(P->device, nb, S, h, kind, P->prec, D.kh)) != LGF_OK) return s;
+            // reflection-reduced tables where the one-CTA-per-chunk products
+            // run (the persistent kernel streams the half table by tensor copies)
+            D.oct = P->symmetric_spectra == 1 && kind != kNear && !uses_persist(P, l);
+            if ((s = get_spectra(P->device, nb, S, h, kind, P->prec, D.kh, D.oct ? 1 : 0)) != LGF_OK) return s;
             D.pp.tmap = D.kh->has_tmap ? &D.kh->tmap : nullptr;
         }
         if (l >= 1 && !(l == 1 && P->merged && Lmac < 2)) {
@@ -1158,7 +1184,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "mac_interval_l2plus", s2, [&] {
                 if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s2);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
-                                        0, table_map(D), P->err, s2);
+                                        0, table_map(D), P->err, s2, D.oct ? 1 : 0, P->mac_gpc);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
         }
@@ -1210,7 +1236,8 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             if (uses_persist(P, 0))
                 return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, early, st);
             return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
-                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, table_map(lev[0]), P->err, st);
+                                    P->S0, P->interval_kernel == 3 ? 3 : 1, 1, table_map(lev[0]), P->err, st,
+                                    lev[0].oct ? 1 : 0, P->mac_gpc);
         });
     } else {
         e = timed(P, "mac_level0", st, [&] {
@@ -1247,7 +1274,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             e = timed(P, "mac_interval_l1", s1, [&] {
                 if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s1);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
-                                        0, table_map(D), P->err, s1);
+                                        0, table_map(D), P->err, s1, D.oct ? 1 : 0, P->mac_gpc);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
             e = timed(P, "c2r_interval", s1, [&] {
@@ -1395,6 +1422,12 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         if (opts->fft_kernel < 0 || opts->fft_kernel > 2)
             return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: fft_kernel must be 0, 1 or 2");
         P->fft_kernel = opts->fft_kernel;
+        if (opts->symmetric_spectra < 0 || opts->symmetric_spectra > 2)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: symmetric_spectra must be 0, 1 or 2");
+        P->symmetric_spectra = opts->symmetric_spectra;
+        if (opts->mac_groups_per_cta < 0 || opts->mac_groups_per_cta > (1 << 20))
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: mac_groups_per_cta must be 0 .. 2^20");
+        P->mac_gpc = opts->mac_groups_per_cta;
         // per-level interpolation orders: entry k is the stencil between
         // parent level k + 2 and level k + 1
         P->nmax_lv.assign(LGF_LEVEL_ORDERS + 2, 0);

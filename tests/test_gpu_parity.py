@@ -333,3 +333,30 @@ def test_irregular_512_manufactured(irregular):
     record_error("tori_irregular_512 manufactured", fp64_vs_exact=fmm.rel_linf(u64, m.u_exact),
                  fp32_vs_exact=fmm.rel_linf(u32, m.u_exact), fp32_vs_fp64=fmm.rel_linf(u32, u64), kappa=k)
     assert np.abs(u32 - u64).max() <= TOL32 * np.abs(ua).max()
+
+
+@pytest.mark.parametrize("case", ["torus96_nb16_L3", "torus128_nb8_L4", "tori_subset_5lev"])
+def test_symmetric_spectra_against_oracle(case, irregular):
+    # reflection-reduced kernel tables (40 representatives instead of the
+    # 172-row half table) at the levels whose products run one CTA per chunk
+    if case == "torus96_nb16_L3":
+        p = W.torus_box(seed=2, nb=6, n_b=16, radius=30.0, sigma=5.0, n_levels=3)
+    elif case == "torus128_nb8_L4":
+        p = W.torus_box(seed=8, nb=16, n_b=8, radius=40.0, sigma=7.0, n_levels=4)
+    else:
+        p = W.block_subset(irregular, 0.08, seed=5, name="tori_subset_512_5lev")
+    ref = oracle_u(p)
+    for prec, tol in ((lgfm.LGF_FP64, TOL64), (lgfm.LGF_FP32, TOL32)):
+        for opts in ({}, {"interval_kernel": 1}):
+            dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+            s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, symmetric_spectra=1, **opts)
+            full = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec, **opts)
+            assert s.workspace_bytes() < full.workspace_bytes()
+            full.close()
+            u = s(torch.from_numpy(p.f).to(dt).cuda())
+            lgfm.lgf_plan_sync(s.plan)
+            err = fmm.rel_linf(u.double().cpu().numpy(), ref)
+            s.close()
+            record_error(f"{case}_symmetric_spectra_{'fp64' if prec == lgfm.LGF_FP64 else 'fp32'}_{opts}",
+                         vs_oracle=err)
+            assert err <= tol, (prec, opts, err)
