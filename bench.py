@@ -495,6 +495,7 @@ def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
             s["without_big_overlap"] = {"requests": sc["requests"], "p50_ms": sc["p50_ms"], "p99_ms": sc["p99_ms"],
                                         "max_ms": sc["max_ms"]}
         s["rejected"] = len(rejected)
+        s["folded_requests"] = srv.folded
         s["plans_resident"] = sum(len(v) for v in srv.pools.slots.values())
         s["hbm_used_gb"] = srv.pools.used / 1e9
         # the same 512^3 request alone: the first run right after the stream
@@ -507,9 +508,11 @@ def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
         # second pass, once the pools hold the plans this load needs
         sat = [Request(r.rid, 0.0, r.key, r.n_points) for r in reqs if n_warm <= r.rid < n_requests]
         srv.run(sat)
+        f0 = srv.folded
         dsat, _ = srv.run(sat)
         ss = summarize(dsat, lambda rid: npts[rid])
-        s["saturated"] = {"points_per_s": ss["points_per_s"], "p50_ms": ss["p50_ms"], "p99_ms": ss["p99_ms"]}
+        s["saturated"] = {"points_per_s": ss["points_per_s"], "p50_ms": ss["p50_ms"], "p99_ms": ss["p99_ms"],
+                          "folded_requests": srv.folded - f0}
         srv.close()
         out[name] = s
     out["config"] = {"workload": "serve_poisson200", "requests_timed": n_requests - n_warm, "warmup": n_warm,

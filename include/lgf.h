@@ -139,23 +139,25 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *                      0 = default.  Supported: n_b = 4: 10; 6: 16; 8: 17,
  *                      18; 10: 24; 12: 28; 14: 32; 16: 33, 34, 36.  The
  *                      level-0 length is 2 n_b.
- *   near_kernel        product kernel of level 0: 0 = default, 1 = fully
- *                      unrolled 4^3-source form, 2 = half-plane pipelined form
+ *   near_kernel        must be 0 (one product kernel for the level-0 near
+ *                      field of the separate form: the 4^3 source blocks of a
+ *                      sibling group, fully unrolled)
  *   interval_kernel    product kernel of levels >= 1 (and of the merged
  *                      level-0/1 pass): 0 = default (5 for FP32 plans where a
  *                      level has >= 48 sibling groups; elsewhere one CTA per
  *                      (frequency chunk, group range) with the packed FP32
  *                      products of form 5, 8 warps), 1 = one frequency per
  *                      thread, one CTA per (frequency chunk, group range), one
- *                      FMA per real product, 2 = two frequencies per
- *                      thread, 3 = two sibling groups per warp sharing
- *                      coefficient loads, 4 = persistent: one CTA per SM,
+ *                      FMA per real product, 3 = two sibling groups per warp
+ *                      sharing coefficient loads (2 is not a form: the two-
+ *                      frequencies-per-thread form lost everywhere and was
+ *                      removed), 4 = persistent: one CTA per SM,
  *                      each taking whole frequency chunks and then an equal
  *                      share of the chunks left over, coefficient chunks
  *                      staged by tensor copies into two shared-memory buffers,
  *                      5 = form 4 with the products as packed two-wide FP32
  *                      FMAs (fma.rn.f32x2), 16 warps per CTA
- *                      (2, 3, 4 and 5: FP32 only; FP64 plans use 1).  A wait
+ *                      (3, 4 and 5: FP32 only; FP64 plans use 1).  A wait
  *                      in forms 4 and 5 that runs out (about 2 s) sets a flag
  *                      that lgf_plan_sync reports as LGF_ERR_CUDA.
  *   single_stream      1 = run every kernel of a solve on the caller's stream;

@@ -124,7 +124,7 @@ def time_options(blocks_list, n_b, levels_list, order, precision, opts, reps=5, 
 
 
 def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = LGF_FP32,
-               use_cache: bool = True, reps: int = 5) -> dict:
+               use_cache: bool = True, reps: int = 10) -> dict:
     """Fastest option set for a set of problems solved as one plan (the cache
     key is the block size, precision, deepest level count and total blocks,
     rounded up to a power of two)."""
@@ -159,7 +159,8 @@ def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = 
             else:
                 trial[name] = v
             ms = measure(trial)
-            if ms is not None and ms < best_ms:
+            # a change must win by more than the timing noise (2%)
+            if ms is not None and ms < 0.98 * best_ms:
                 best_ms, best = ms, trial
     if use_cache:
         with _LOCK:
@@ -171,6 +172,6 @@ def tune_multi(blocks_list, n_b: int, levels_list, order: int, precision: int = 
 
 
 def tune(blocks, n_b: int, n_levels: int, order: int, precision: int = LGF_FP32,
-         use_cache: bool = True, reps: int = 5) -> dict:
+         use_cache: bool = True, reps: int = 10) -> dict:
     """Fastest option set for one problem (from the cache when present)."""
     return tune_multi([np.asarray(blocks).reshape(-1, 3)], n_b, [n_levels], order, precision, use_cache, reps)

@@ -39,12 +39,50 @@ __device__ __forceinline__ cx<double> ldg_cx<double>(const cx<double>* p) {
 }
 
 constexpr int kFftThreads = 256;
+// Items (blocks or intervals) per CTA of the per-block transforms: small
+// transforms share a CTA, so that its passes have lines for its threads (the
+// level-0 transform of n_b = 8 has 9 x 8 y-lines: four blocks per CTA give
+// 288).  A pass of one line per thread takes as many rounds as its lines
+// need: with 256 threads the level-0 transform of n_b = 16 (17 x 16 y-lines,
+// 17 x 32 z-lines) runs 2 + 3 rounds, with 272 threads 1 + 2.
+template <typename T, int S, int N>
+__host__ __device__ constexpr int fft_items_per_cta() {
+    constexpr int y_lines = (S / 2 + 1) * N;
+    int k = 1;
+    while (2 * k * y_lines <= 320 && k < 16) k *= 2;
+    return k;
+}
+// CTA size: one round of the y pass where that is at most 288 lines (two CTAs
+// per SM for FP32: their registers are capped accordingly, 120 per thread at
+// 272), else 256.
+template <typename T, int S, int N>
+__host__ __device__ constexpr int fft_threads() {
+    constexpr int lines = fft_items_per_cta<T, S, N>() * (S / 2 + 1) * N;
+    return lines <= 288 ? ((lines + 31) / 32 * 32 < 128 ? 128 : (lines + 31) / 32 * 32) : kFftThreads;
+}
+template <typename T, int S, int N>
+__host__ __device__ constexpr int fft_min_blocks() {
+    return sizeof(T) == 4 && fft_threads<T, S, N>() > kFftThreads ? 2 : 1;
+}
 
-// Shared-memory footprint of the FFT kernels (bytes): the partially
-// transformed cube with an odd row pitch, plus the staged real cube.
+// FP32 cubes whose rows are whole 16-byte vectors move between global memory
+// and the x pass directly (each thread its own rows, 16-byte loads/stores),
+// with no staged real cube in shared memory.
+template <typename T, int N>
+__host__ __device__ constexpr bool fft_direct_rows() {
+    return sizeof(T) == 4 && N % 4 == 0;
+}
+// Shared-memory footprint of one item of the FFT kernels (bytes): the
+// partially transformed cube with an odd row pitch, plus the staged real cube;
+// and of a CTA (its items)
+template <typename T, int S, int N>
+__host__ __device__ constexpr size_t fft_item_smem() {
+    return sizeof(cx<T>) * size_t(N) * ((S * ((S / 2 + 1) | 1)) | 1) +
+           (fft_direct_rows<T, N>() ? 0 : sizeof(T) * size_t(N) * N * (N | 1));
+}
 template <typename T, int S, int N>
 __host__ __device__ constexpr size_t fft_smem_bytes() {
-    return sizeof(cx<T>) * size_t(N) * ((S * ((S / 2 + 1) | 1)) | 1) + sizeof(T) * size_t(N) * N * (N | 1);
+    return fft_items_per_cta<T, S, N>() * fft_item_smem<T, S, N>();
 }
 
 // copy n reals (n % 4 == 0) with 16-byte vectors when both ends are aligned
@@ -72,51 +110,90 @@ __device__ __forceinline__ void staged_copy(int n, const T* src, F&& put) {
 // NXP = NX rounded up to odd, so one-line-per-thread passes are free of bank
 // conflicts; the last pass goes straight to global memory.
 template <typename T, int S, int NIN>
-__global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, int64_t src_stride,
-                                                     const R2CItem* __restrict__ items,
-                                                     cx<T>* __restrict__ spec) {
+__global__ void __launch_bounds__(fft_threads<T, S, NIN>(), fft_min_blocks<T, S, NIN>())
+    k_r2c(const T* __restrict__ src, int64_t src_stride, const R2CItem* __restrict__ items,
+          cx<T>* __restrict__ spec, int n_items) {
     constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NIN | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
+    constexpr int K = fft_items_per_cta<T, S, NIN>();
+    constexpr size_t ITEM = fft_item_smem<T, S, NIN>();
+    constexpr bool DIRECT = fft_direct_rows<T, NIN>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
-    T* X = reinterpret_cast<T*>(B + NIN * PP);
-    const R2CItem it = items[blockIdx.x];
-    const T* in = src + int64_t(it.src) * src_stride;
-    cx<T>* out = spec + int64_t(it.dst) * NWS;
+    const int first = blockIdx.x * K;
+    const int nk = min(K, n_items - first);   // items of this CTA
+    // item b's partially transformed cube and staged input
+    auto Bof = [&](int b) { return reinterpret_cast<cx<T>*>(smem_raw + b * ITEM); };
+    auto Xof = [&](int b) { return reinterpret_cast<T*>(Bof(b) + NIN * PP); };
+    auto in_of = [&](int b) { return src + int64_t(items[first + b].src) * src_stride; };
     // a kernel launched after this one with programmatic serialization (the
     // level-0 products) may start its prologue once every CTA got here; it
     // waits for this grid to finish before it reads the spectra
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    staged_copy<T>(NIN * NIN * NIN, in, [&](int i, T v) { X[(i / NIN) * RS + i % NIN] = v; });
-    __syncthreads();
+    if constexpr (!DIRECT) {
+        for (int b = 0; b < nk; ++b) {
+            T* X = Xof(b);
+            staged_copy<T>(NIN * NIN * NIN, in_of(b), [&](int i, T v) { X[(i / NIN) * RS + i % NIN] = v; });
+        }
+        __syncthreads();
+    }
     // x pass: lines l and l + NP (rows of the (y, z) plane) as one complex transform
     constexpr int NL = NIN * NIN, NP = (NL + 1) / 2;
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-        const int l0 = p, l1 = p + NP;
+    for (int p = threadIdx.x; p < nk * NP; p += blockDim.x) {
+        const int b = p / NP, l0 = p % NP, l1 = l0 + NP;
         const bool has1 = l1 < NL;
-        const T* r0 = X + l0 * RS;
-        const T* r1 = X + (has1 ? l1 : l0) * RS;
+        cx<T>* B = Bof(b);
         cx<T> z[S];
+        if constexpr (DIRECT) {
+            // the two rows straight from global memory, 16-byte vectors when
+            // the cube is 16-byte aligned (a caller's buffer may not be)
+            const T* in = in_of(b);
+            T a[NIN], c[NIN];
+            const T* q0 = in + int64_t(l0) * NIN;
+            const T* q1 = in + int64_t(has1 ? l1 : l0) * NIN;
+            if ((reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+                const float4* g0 = reinterpret_cast<const float4*>(q0);
+                const float4* g1 = reinterpret_cast<const float4*>(q1);
 #pragma unroll
-        for (int x = 0; x < S; ++x)
-            z[x] = x < NIN ? cx<T>{r0[x], has1 ? r1[x] : T(0)} : czero<T>();
+                for (int q = 0; q < NIN / 4; ++q) {
+                    const float4 u = __ldg(g0 + q), v = __ldg(g1 + q);
+                    a[4 * q] = u.x; a[4 * q + 1] = u.y; a[4 * q + 2] = u.z; a[4 * q + 3] = u.w;
+                    c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int x = 0; x < NIN; ++x) {
+                    a[x] = __ldg(q0 + x);
+                    c[x] = __ldg(q1 + x);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < S; ++x) z[x] = x < NIN ? cx<T>{a[x], has1 ? c[x] : T(0)} : czero<T>();
+        } else {
+            const T* X = Xof(b);
+            const T* r0 = X + l0 * RS;
+            const T* r1 = X + (has1 ? l1 : l0) * RS;
+#pragma unroll
+            for (int x = 0; x < S; ++x)
+                z[x] = x < NIN ? cx<T>{r0[x], has1 ? r1[x] : T(0)} : czero<T>();
+        }
         fft<S, S, -1, NIN>(z);
         const int y0 = l0 % NIN, z0 = l0 / NIN, y1 = l1 % NIN, z1 = l1 / NIN;
         cx<T>* d0 = B + z0 * PP + y0 * NXP;
         cx<T>* d1 = B + z1 * PP + y1 * NXP;
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
-            const cx<T> a = z[k], b = z[(S - k) % S];
-            d0[k] = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
-            if (has1) d1[k] = {T(0.5) * (a.y + b.y), T(0.5) * (b.x - a.x)};
+            const cx<T> u = z[k], v = z[(S - k) % S];
+            d0[k] = {T(0.5) * (u.x + v.x), T(0.5) * (u.y - v.y)};
+            if (has1) d1[k] = {T(0.5) * (u.y + v.y), T(0.5) * (v.x - u.x)};
         }
     }
     __syncthreads();
     // y pass: lines (kx, z), in place within the column
-    for (int l = threadIdx.x; l < NX * NIN; l += blockDim.x) {
+    for (int q = threadIdx.x; q < nk * NX * NIN; q += blockDim.x) {
+        const int b = q / (NX * NIN), l = q % (NX * NIN);
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * PP + kx;
+        cx<T>* col = Bof(b) + zz * PP + kx;
         cx<T> v[S];
 #pragma unroll
         for (int y = 0; y < S; ++y) v[y] = y < NIN ? col[y * NXP] : czero<T>();
@@ -126,9 +203,11 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
     }
     __syncthreads();
     // z pass: lines (kx, ky), results to global (coalesced across the CTA)
-    for (int l = threadIdx.x; l < NX * S; l += blockDim.x) {
+    for (int q = threadIdx.x; q < nk * NX * S; q += blockDim.x) {
+        const int b = q / (NX * S), l = q % (NX * S);
         const int kx = l % NX, ky = l / NX;
-        const cx<T>* col = B + ky * NXP + kx;
+        const cx<T>* col = Bof(b) + ky * NXP + kx;
+        cx<T>* out = spec + int64_t(items[first + b].dst) * NWS;
         cx<T> v[S];
 #pragma unroll
         for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * PP] : czero<T>();
@@ -146,35 +225,44 @@ __global__ void __launch_bounds__(kFftThreads) k_r2c(const T* __restrict__ src, 
 // result cube is staged in shared memory (odd row pitch) and written with
 // coalesced stores.
 template <typename T, int S, int NOUT>
-__global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ spec,
-                                                     const C2RItem* __restrict__ items,
-                                                     T* __restrict__ dst, int64_t dst_stride,
-                                                     const T* __restrict__ add, int add_n,
-                                                     int64_t add_stride) {
+__global__ void __launch_bounds__(fft_threads<T, S, NOUT>(), fft_min_blocks<T, S, NOUT>())
+    k_c2r(const cx<T>* __restrict__ spec, const C2RItem* __restrict__ items, T* __restrict__ dst,
+          int64_t dst_stride, const T* __restrict__ add, int add_n, int64_t add_stride, int n_items) {
     constexpr int NX = S / 2 + 1, NXP = NX | 1, RS = NOUT | 1, PP = (S * NXP) | 1;
     constexpr int64_t NWS = (int64_t(NX) * S * S + 31) / 32 * 32;
+    constexpr int K = fft_items_per_cta<T, S, NOUT>();
+    constexpr size_t ITEM = fft_item_smem<T, S, NOUT>();
+    constexpr bool DIRECT = fft_direct_rows<T, NOUT>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cx<T>* B = reinterpret_cast<cx<T>*>(smem_raw);
-    T* O = reinterpret_cast<T*>(B + NOUT * PP);
-    const C2RItem it = items[blockIdx.x];
-    const cx<T>* in = spec + int64_t(it.src) * NWS;
+    const int first = blockIdx.x * K;
+    const int nk = min(K, n_items - first);   // items of this CTA
+    auto Bof = [&](int b) { return reinterpret_cast<cx<T>*>(smem_raw + b * ITEM); };
+    auto Oof = [&](int b) { return reinterpret_cast<T*>(Bof(b) + NOUT * PP); };
+    auto out_of = [&](int b) { return dst + int64_t(items[first + b].dst) * dst_stride; };
+    auto add_of = [&](int b) -> const T* {
+        const int aux = items[first + b].aux;
+        return (add != nullptr && aux >= 0) ? add + int64_t(aux) * add_stride : nullptr;
+    };
 
     // z pass: lines (kx, ky); keep z < NOUT
-    for (int l = threadIdx.x; l < NX * S; l += blockDim.x) {
+    for (int q = threadIdx.x; q < nk * NX * S; q += blockDim.x) {
+        const int b = q / (NX * S), l = q % (NX * S);
         const int kx = l % NX, ky = l / NX;
+        const cx<T>* in = spec + int64_t(items[first + b].src) * NWS;
         cx<T> v[S];
 #pragma unroll
         for (int kz = 0; kz < S; ++kz) v[kz] = ldg_cx(in + int64_t(kz) * S * NX + l);
         fft<S, S, 1, S>(v);
-        cx<T>* col = B + ky * NXP + kx;
+        cx<T>* col = Bof(b) + ky * NXP + kx;
 #pragma unroll
         for (int zz = 0; zz < NOUT; ++zz) col[zz * PP] = v[zz];
     }
     __syncthreads();
     // y pass: lines (kx, z < NOUT); keep y < NOUT
-    for (int l = threadIdx.x; l < NX * NOUT; l += blockDim.x) {
+    for (int q = threadIdx.x; q < nk * NX * NOUT; q += blockDim.x) {
+        const int b = q / (NX * NOUT), l = q % (NX * NOUT);
         const int kx = l % NX, zz = l / NX;
-        cx<T>* col = B + zz * PP + kx;
+        cx<T>* col = Bof(b) + zz * PP + kx;
         cx<T> v[S];
 #pragma unroll
         for (int y = 0; y < S; ++y) v[y] = col[y * NXP];
@@ -185,16 +273,17 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
     __syncthreads();
     // x pass: two Hermitian half-lines (rows l and l + NP) per complex inverse
     constexpr int NL = NOUT * NOUT, NP = (NL + 1) / 2;
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-        const int l0 = p, l1 = p + NP;
+    for (int p = threadIdx.x; p < nk * NP; p += blockDim.x) {
+        const int b = p / NP, l0 = p % NP, l1 = l0 + NP;
         const bool has1 = l1 < NL;
+        const cx<T>* B = Bof(b);
         const int y0 = l0 % NOUT, z0 = l0 / NOUT, y1 = l1 % NOUT, z1 = l1 / NOUT;
-        const cx<T>* a = B + z0 * PP + y0 * NXP;
-        const cx<T>* b = B + (has1 ? z1 : z0) * PP + (has1 ? y1 : y0) * NXP;
+        const cx<T>* ra = B + z0 * PP + y0 * NXP;
+        const cx<T>* rb = B + (has1 ? z1 : z0) * PP + (has1 ? y1 : y0) * NXP;
         cx<T> z[S];
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
-            cx<T> A = a[k], Bk = has1 ? b[k] : czero<T>();
+            cx<T> A = ra[k], Bk = has1 ? rb[k] : czero<T>();
             if (k == 0 || 2 * k == S) {   // exactly real for a real signal
                 A.y = T(0);
                 Bk.y = T(0);
@@ -203,35 +292,55 @@ __global__ void __launch_bounds__(kFftThreads) k_c2r(const cx<T>* __restrict__ s
             if (k > 0 && S - k >= NX) z[S - k] = {A.x + Bk.y, Bk.x - A.y};
         }
         fft<S, S, 1, S>(z);
+        if constexpr (DIRECT) {
+            // the two rows straight to global memory (plus the level-1 field),
+            // 16-byte vectors when the output is 16-byte aligned
+            T* out = out_of(b);
+            const T* ad = add_of(b);
+            const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
 #pragma unroll
-        for (int x = 0; x < NOUT; ++x) {
-            O[l0 * RS + x] = z[x].x;
-            if (has1) O[l1 * RS + x] = z[x].y;
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !has1) break;
+                const int l = h == 0 ? l0 : l1;
+                T v[NOUT];
+#pragma unroll
+                for (int x = 0; x < NOUT; ++x) v[x] = h == 0 ? z[x].x : z[x].y;
+                if (ad) {
+                    const T* a = ad + ((l / NOUT) * add_n + l % NOUT) * add_n;
+#pragma unroll
+                    for (int x = 0; x < NOUT; ++x) v[x] += __ldg(a + x);
+                }
+                T* o = out + int64_t(l) * NOUT;
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < NOUT / 4; ++q)
+                        reinterpret_cast<float4*>(o)[q] = make_float4(float(v[4 * q]), float(v[4 * q + 1]),
+                                                                      float(v[4 * q + 2]), float(v[4 * q + 3]));
+                } else {
+#pragma unroll
+                    for (int x = 0; x < NOUT; ++x) o[x] = v[x];
+                }
+            }
+        } else {
+            T* O = Oof(b);
+#pragma unroll
+            for (int x = 0; x < NOUT; ++x) {
+                O[l0 * RS + x] = z[x].x;
+                if (has1) O[l1 * RS + x] = z[x].y;
+            }
         }
     }
-    __syncthreads();
-    T* out = dst + int64_t(it.dst) * dst_stride;
-    const T* ad = (add != nullptr && it.aux >= 0) ? add + int64_t(it.aux) * add_stride : nullptr;
-    constexpr int N3 = NOUT * NOUT * NOUT;
-    if (sizeof(T) == 4 && NOUT % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        for (int i = threadIdx.x; i < N3 / 4; i += blockDim.x) {
-            const int x = (4 * i) % NOUT, yz = (4 * i) / NOUT;
-            T v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = O[yz * RS + x + j];
-            if (ad) {
-                const T* a = ad + ((yz / NOUT) * add_n + yz % NOUT) * add_n + x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] += a[j];
-            }
-            reinterpret_cast<float4*>(out)[i] = make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3]));
-        }
-    } else {
-        for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    if constexpr (!DIRECT) {
+        // the staged cubes out with coalesced stores, plus the level-1 field
+        __syncthreads();
+        constexpr int N3 = NOUT * NOUT * NOUT;
+        for (int q = threadIdx.x; q < nk * N3; q += blockDim.x) {
+            const int b = q / N3, i = q % N3;
             const int x = i % NOUT, yz = i / NOUT;
-            T v = O[yz * RS + x];
+            const T* ad = add_of(b);
+            T v = Oof(b)[yz * RS + x];
             if (ad) v += ad[((yz / NOUT) * add_n + yz % NOUT) * add_n + x];
-            out[i] = v;
+            out_of(b)[i] = v;
         }
     }
 }
@@ -690,237 +799,6 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? 2 : 1) k_mac_inte
         if (more) mac_load<T, S>(Fa, fh, gnbr, nxt, wc);
         if (cur.e >= 0) block(Fb, cur.e);
         if (!more || nxt.g != cur.g) flush(cur.gid);
-        if (!more) break;
-        cur = nxt;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Level-0 near-field products, pipelined form.  Same work as k_mac_level0; the
-// 4^3 source blocks around the group are taken in 8 half-planes (fixed tz,
-// two ty rows, four tx) and the 8 spectra of the next half-plane are loaded
-// while the products of the current one run, so loads stay in flight with
-// few registers.  S is a template parameter so every offset is a constant.
-template <typename T, int S>
-__device__ __forceinline__ void mac0_load(cx<T> (&F)[8], const cx<T>* __restrict__ fh, const int (&q)[27],
-                                          int step, int64_t w) {
-    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
-    const int tz = step / 2 - 1;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int tx = (k & 3) - 1, ty = 2 * (step & 1) - 1 + (k >> 2);
-        const int ex = tx < 0 ? -1 : tx >> 1, ey = ty < 0 ? -1 : ty >> 1, ez = tz < 0 ? -1 : tz >> 1;
-        const int qq = q[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
-        const int cs = (tx - 2 * ex) + 2 * (ty - 2 * ey) + 4 * (tz - 2 * ez);
-        F[k] = qq >= 0 ? ldg_cx(fh + (int64_t(qq) * 8 + cs) * NWS + w) : czero<T>();
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void mac0_block(cx<T> (&acc)[8], const cx<T> (&F)[8], const cx<T> (&k)[27], int step) {
-    const int tz = step / 2 - 1;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-        const int tx = (kk & 3) - 1, ty = 2 * (step & 1) - 1 + (kk >> 2);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int dx = tx - (c & 1), dy = ty - ((c >> 1) & 1), dz = tz - (c >> 2);
-            if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-            acc[c] = cmac(acc[c], F[kk], k[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]);
-        }
-    }
-}
-
-template <typename T, int S>
-__global__ void __launch_bounds__(256, 2) k_mac_level0_pipe(const cx<T>* __restrict__ fh,
-                                                            const cx<T>* __restrict__ kh,
-                                                            cx<T>* __restrict__ uh,
-                                                            const int* __restrict__ gnbr, int n_groups) {
-    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
-    constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    const int64_t w = int64_t(blockIdx.y) * 32 + threadIdx.x;
-    const int g = blockIdx.x * blockDim.y + threadIdx.y;
-    if (g >= n_groups || w >= NW) return;
-    int q[27];
-#pragma unroll
-    for (int e = 0; e < 27; ++e) q[e] = __ldg(gnbr + int64_t(g) * 27 + e);
-    cx<T> Fa[8], Fb[8];
-    mac0_load<T, S>(Fa, fh, q, 0, w);
-    cx<T> k[27];
-#pragma unroll
-    for (int d = 0; d < 27; ++d) k[d] = ldg_cx(kh + d * NWS + w);
-    cx<T> acc[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = czero<T>();
-#pragma unroll
-    for (int step = 0; step < 8; step += 2) {
-        mac0_load<T, S>(Fb, fh, q, step + 1, w);
-        mac0_block(acc, Fa, k, step);
-        if (step + 2 < 8) mac0_load<T, S>(Fa, fh, q, step + 2, w);
-        mac0_block(acc, Fb, k, step + 1);
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) uh[(int64_t(g) * 8 + c) * NWS + w] = acc[c];
-}
-
-// ---------------------------------------------------------------------------
-// Interaction-list products with two frequencies per thread: 128-bit loads of
-// source spectra and coefficients, half the load and address instructions per
-// FMA of k_mac_interval.  A CTA of kMac2Warps warps covers 64 frequencies; the
-// 343 coefficient rows of those frequencies fill shared memory (176 KB FP32),
-// so one CTA runs per SM.
-constexpr int kMac2Warps = 16;
-
-template <typename T>
-struct cx2 {
-    cx<T> a, b;
-};
-
-template <typename T>
-__device__ __forceinline__ cx2<T> ld2(const cx<T>* p) {
-    cx2<T> r;
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        r.a = {v.x, v.y};
-        r.b = {v.z, v.w};
-    } else {
-        r.a = ldg_cx(p);
-        r.b = ldg_cx(p + 1);
-    }
-    return r;
-}
-
-template <typename T>
-__device__ __forceinline__ cx2<T> lds2(const cx<T>* p) {
-    cx2<T> r;
-    r.a = p[0];
-    r.b = p[1];
-    return r;
-}
-// FP32: both values in one 16-byte load
-template <>
-__device__ __forceinline__ cx2<float> lds2<float>(const cx<float>* p) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    cx2<float> r;
-    r.a = {v.x, v.y};
-    r.b = {v.z, v.w};
-    return r;
-}
-
-struct MacWalk2 {
-    int g, e;
-    unsigned mask;
-};
-
-__device__ __forceinline__ bool mac2_next(MacWalk2& it, const int* __restrict__ gnbr, int g1) {
-    if (it.mask) {
-        it.e = __ffs(it.mask) - 1;
-        it.mask &= it.mask - 1;
-        return true;
-    }
-    it.g += kMac2Warps;
-    if (it.g >= g1) return false;
-    it.mask = nbr_mask(gnbr, it.g);
-    if (it.mask) {
-        it.e = __ffs(it.mask) - 1;
-        it.mask &= it.mask - 1;
-    } else {
-        it.e = -1;
-    }
-    return true;
-}
-
-template <typename T, int S>
-__device__ __forceinline__ void mac2_load(cx2<T> (&F)[8], const cx<T>* __restrict__ fh,
-                                          const int* __restrict__ gnbr, const MacWalk2& it, int64_t wc) {
-    constexpr int64_t NWS = (int64_t(S / 2 + 1) * S * S + 31) / 32 * 32;
-    if (it.e < 0) return;
-    const cx<T>* src = fh + int64_t(__ldg(gnbr + int64_t(it.g) * 27 + it.e)) * (8 * NWS) + wc;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) F[c] = ld2(src + c * NWS);
-}
-
-template <typename T>
-__device__ __forceinline__ void mac2_block(cx2<T> (&acc)[8], const cx2<T> (&F)[8], const cx<T>* __restrict__ sk,
-                                           int e) {
-    const int ex = e % 3, ey = (e / 3) % 3, ez = e / 9;
-    const cx<T>* kb = sk + ((2 * ex + 1) + 7 * (2 * ey + 1) + 49 * (2 * ez + 1)) * 64 + 2 * threadIdx.x;
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const cx2<T> kk = lds2(kb + (dx + 7 * dy + 49 * dz) * 64);
-#pragma unroll
-                for (int ct = 0; ct < 8; ++ct) {
-                    const int cx_ = (ct & 1) + dx, cy_ = ((ct >> 1) & 1) + dy, cz_ = (ct >> 2) + dz;
-                    if (cx_ < 0 || cx_ > 1 || cy_ < 0 || cy_ > 1 || cz_ < 0 || cz_ > 1) continue;
-                    const int cs = cx_ + 2 * cy_ + 4 * cz_;
-                    acc[ct].a = cmac(acc[ct].a, F[cs].a, kk.a);
-                    acc[ct].b = cmac(acc[ct].b, F[cs].b, kk.b);
-                }
-            }
-}
-
-template <typename T, int S>
-__device__ __forceinline__ void mac2_store(cx2<T> (&acc)[8], cx<T>* __restrict__ uh, int g, int64_t w) {
-    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
-    constexpr int64_t NWS = (NW + 31) / 32 * 32;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        cx<T>* o = uh + (int64_t(g) * 8 + c) * NWS + w;
-        if (w < NW) o[0] = acc[c].a;
-        if (w + 1 < NW) o[1] = acc[c].b;
-        acc[c].a = czero<T>();
-        acc[c].b = czero<T>();
-    }
-}
-
-template <typename T, int S>
-__global__ void __launch_bounds__(32 * kMac2Warps, 1) k_mac_interval2(const cx<T>* __restrict__ fh,
-                                                                     const cx<T>* __restrict__ kh,
-                                                                     cx<T>* __restrict__ uh,
-                                                                     const int* __restrict__ gnbr, int n_groups,
-                                                                     int groups_per_cta) {
-    constexpr int64_t NW = int64_t(S / 2 + 1) * S * S;
-    constexpr int64_t NWS = (NW + 31) / 32 * 32;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cx<T>* sk = reinterpret_cast<cx<T>*>(smem_raw);   // [343][64]
-    const int64_t w0 = int64_t(blockIdx.y) * 64;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < 343 * 64; i += 32 * kMac2Warps) {
-        const int d = i >> 6, lane = i & 63;
-        const int64_t w = w0 + lane;
-        sk[i] = w < NW ? coef_sym<T, NWS>(kh, d, w) : czero<T>();
-    }
-    __syncthreads();
-    const int g0 = blockIdx.x * groups_per_cta;
-    const int g1 = min(n_groups, g0 + groups_per_cta);
-    const int64_t w = w0 + 2 * threadIdx.x;
-    // the pair (w, w+1) is read as one 16-byte vector; w is even and the
-    // spectrum stride NWS is a multiple of 32, so the vector is aligned; past
-    // the end of the spectrum the read is clamped into the padded stride
-    const int64_t wc = w < NWS - 2 ? w : NWS - 2;
-    MacWalk2 cur{g0 + int(threadIdx.y) - kMac2Warps, -1, 0u};
-    if (!mac2_next(cur, gnbr, g1)) return;
-    cx2<T> Fa[8], Fb[8], acc[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = {czero<T>(), czero<T>()};
-    mac2_load<T, S>(Fa, fh, gnbr, cur, wc);
-    while (true) {
-        MacWalk2 nxt = cur;
-        bool more = mac2_next(nxt, gnbr, g1);
-        if (more) mac2_load<T, S>(Fb, fh, gnbr, nxt, wc);
-        if (cur.e >= 0) mac2_block(acc, Fa, sk, cur.e);
-        if (!more || nxt.g != cur.g) mac2_store<T, S>(acc, uh, cur.g, w);
-        if (!more) break;
-        cur = nxt;
-        nxt = cur;
-        more = mac2_next(nxt, gnbr, g1);
-        if (more) mac2_load<T, S>(Fa, fh, gnbr, nxt, wc);
-        if (cur.e >= 0) mac2_block(acc, Fb, sk, cur.e);
-        if (!more || nxt.g != cur.g) mac2_store<T, S>(acc, uh, cur.g, w);
         if (!more) break;
         cur = nxt;
     }
@@ -2127,7 +2005,9 @@ static cudaError_t launch_r2c(const T* src, int64_t stride, const R2CItem* items
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    k<<<n, dev::kFftThreads, smem, st>>>(src, stride, items, static_cast<dev::cx<T>*>(spec));
+    constexpr int K = dev::fft_items_per_cta<T, S, NIN>();
+    k<<<(n + K - 1) / K, dev::fft_threads<T, S, NIN>(), smem, st>>>(src, stride, items,
+                                                                     static_cast<dev::cx<T>*>(spec), n);
     return cudaGetLastError();
 }
 
@@ -2139,8 +2019,9 @@ static cudaError_t launch_c2r(const void* spec, const C2RItem* items, int n, T* 
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    k<<<n, dev::kFftThreads, smem, st>>>(static_cast<const dev::cx<T>*>(spec), items, dst, ds, add,
-                                         add_n, as);
+    constexpr int K = dev::fft_items_per_cta<T, S, NOUT>();
+    k<<<(n + K - 1) / K, dev::fft_threads<T, S, NOUT>(), smem, st>>>(static_cast<const dev::cx<T>*>(spec), items,
+                                                                      dst, ds, add, add_n, as, n);
     return cudaGetLastError();
 }
 
@@ -2169,39 +2050,19 @@ cudaError_t Launch<T>::c2r(int S, int n_out, const void* spec, const C2RItem* it
     return LaunchExt<T>::c2r(S, n_out, spec, items, n, dst, ds, add, add_n, as, st);
 }
 
-template <typename T, int S>
-static cudaError_t launch_mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
-                                     int variant, cudaStream_t st) {
-    if (n_groups == 0) return cudaSuccess;
-    const int64_t NW = nw_of(S), NWS = nws_of(S);
-    const int G = 8;
-    dim3 block(32, G), grid((n_groups + G - 1) / G, unsigned((NW + 31) / 32));
-    const auto* f = static_cast<const dev::cx<T>*>(fh);
-    const auto* k = static_cast<const dev::cx<T>*>(kh);
-    auto* u = static_cast<dev::cx<T>*>(uh);
-    if (variant == 1) dev::k_mac_level0<T><<<grid, block, 0, st>>>(f, k, u, gnbr, n_groups, NW, NWS);
-    else dev::k_mac_level0_pipe<T, S><<<grid, block, 0, st>>>(f, k, u, gnbr, n_groups);
-    return cudaGetLastError();
-}
-
+// The near-field products of the separate level-0 form (Sec. 3.1 lists): one
+// kernel for every transform length, the spectrum size a run-time argument.
 template <typename T>
 cudaError_t Launch<T>::mac_level0(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups,
                                   int S, int variant, cudaStream_t st) {
-    switch (S) {
-        case 8: return launch_mac_level0<T, 8>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 16: return launch_mac_level0<T, 16>(fh, kh, uh, gnbr, n_groups, variant, st);
-        case 32: return launch_mac_level0<T, 32>(fh, kh, uh, gnbr, n_groups, variant, st);
-        default: {
-            // other lengths: the first form, whose spectrum size is a run-time argument
-            if (n_groups == 0) return cudaSuccess;
-            const int64_t NW = nw_of(S), NWS = nws_of(S);
-            dim3 block(32, 8), grid((n_groups + 7) / 8, unsigned((NW + 31) / 32));
-            dev::k_mac_level0<T><<<grid, block, 0, st>>>(static_cast<const dev::cx<T>*>(fh),
-                                                         static_cast<const dev::cx<T>*>(kh),
-                                                         static_cast<dev::cx<T>*>(uh), gnbr, n_groups, NW, NWS);
-            return cudaGetLastError();
-        }
-    }
+    (void)variant;
+    if (n_groups == 0) return cudaSuccess;
+    const int64_t NW = nw_of(S), NWS = nws_of(S);
+    dim3 block(32, 8), grid((n_groups + 7) / 8, unsigned((NW + 31) / 32));
+    dev::k_mac_level0<T><<<grid, block, 0, st>>>(static_cast<const dev::cx<T>*>(fh),
+                                                 static_cast<const dev::cx<T>*>(kh), static_cast<dev::cx<T>*>(uh),
+                                                 gnbr, n_groups, NW, NWS);
+    return cudaGetLastError();
 }
 
 template <typename T, int S>
@@ -2223,8 +2084,8 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
             per *= 2;
         return per;
     };
-    if (include_self && variant == 2) variant = 1;
-    if (oct && (variant == 2 || variant == 3)) variant = 1;   // those stage the half table themselves
+    if (variant == 2) variant = 1;                            // (the two-frequency form was removed)
+    if (oct && variant == 3) variant = 1;                     // it stages the half table itself
     if (variant == 3 && sizeof(T) == 4) {
         const size_t smem = sizeof(dev::cx<T>) * 343 * 32;
         auto kern = dev::k_mac_interval_pair<T, S>;
@@ -2235,20 +2096,6 @@ static cudaError_t launch_mac_interval(const void* fh, const void* kh, void* uh,
         int per = groups_per_cta(2 * dev::kMacPWarps, 1, nchunks);
         dim3 block(32, dev::kMacPWarps), grid((n_groups + per - 1) / per, unsigned(nchunks));
         kern<<<grid, block, smem, st>>>(f, k, u, gnbr, order, n_groups, per, include_self);
-        return cudaGetLastError();
-    }
-    // two frequencies per thread need 343 x 64 coefficients in shared memory:
-    // 176 KB in FP32, too much in FP64, which keeps the one-frequency form
-    if (variant == 2 && sizeof(T) == 4) {
-        const size_t smem = sizeof(dev::cx<T>) * 343 * 64;
-        auto kern = dev::k_mac_interval2<T, S>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        if (n_groups == 0) return cudaSuccess;
-        const int64_t nchunks = (NW + 63) / 64;
-        const int per = groups_per_cta(dev::kMac2Warps, 1, nchunks);
-        dim3 block(32, dev::kMac2Warps), grid((n_groups + per - 1) / per, unsigned(nchunks));
-        kern<<<grid, block, smem, st>>>(f, k, u, gnbr, n_groups, per);
         return cudaGetLastError();
     }
     // FP32 outside variant 1: packed two-wide FMAs, 8 warps of up to 128

@@ -1411,8 +1411,9 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
         P->SI = opts->fft_size_interval;
     }
     if (opts) {
-        if (opts->near_kernel < 0 || opts->near_kernel > 2 || opts->interval_kernel < 0 || opts->interval_kernel > 5)
-            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0..2 and interval_kernel 0..5");
+        if (opts->near_kernel != 0 || opts->interval_kernel < 0 || opts->interval_kernel > 5 ||
+            opts->interval_kernel == 2)
+            return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: near_kernel must be 0 and interval_kernel 0, 1, 3, 4 or 5");
         P->near_kernel = opts->near_kernel;
         P->interval_kernel = opts->interval_kernel;
         P->single_stream = opts->single_stream != 0;

@@ -160,15 +160,43 @@ class PlanPools:
 
 
 def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter, max_inflight: int = 64,
-               need_bytes=None, idle_wait: float = 20e-6, sleep=time.sleep):
-    """Drive a request stream.  submit(slot, request) starts the work and
-    returns a token; poll(token) -> bool says whether it finished.
-    need_bytes(key) (optional) estimates a new plan's bytes before creating it.
+               need_bytes=None, idle_wait: float = 20e-6, sleep=time.sleep, fold=None):
+    """Drive a request stream.  submit(slot, requests) starts the work of a
+    list of requests on one plan and returns a token; poll(token) -> bool says
+    whether it finished.  need_bytes(key) (optional) estimates a new plan's
+    bytes before creating it.  fold(key) (optional) gives the largest number
+    of requests of one shape to solve together: when several requests of a
+    shape are pending at the same moment they take one plan of key (key, k),
+    k a power of two (a multi-problem plan, one launch per phase for all k),
+    if one is idle or can be made, else they run one by one.
     Returns the list of Done records and the rejected request ids."""
     pending = sorted(requests, key=lambda r: r.arrival)
     inflight = []
     done, rejected = [], []
     t0 = clock()
+
+    def try_fold(i, now, allow_new):
+        """A folded plan for pending[i] and the arrived requests of its shape
+        behind it: (slot, indices) or None."""
+        kmax = fold(pending[i].key) if fold else 1
+        if kmax < 2:
+            return None
+        same = [j for j in range(i, len(pending))
+                if pending[j].arrival <= now and pending[j].key == pending[i].key][:kmax]
+        k = 1
+        while 2 * k <= len(same):
+            k *= 2
+        while k >= 2:
+            key = (pending[i].key, k)
+            try:
+                slot = pools.acquire(key, now, need_bytes(key) if need_bytes else None, allow_new=allow_new)
+            except AdmissionError:
+                slot = None
+            if slot is not None:
+                return slot, same[:k]
+            k //= 2
+        return None
+
     while pending or inflight:
         now = clock() - t0
         progressed = False
@@ -177,6 +205,16 @@ def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter
         i, waiting = 0, False
         while i < len(pending) and pending[i].arrival <= now and len(inflight) < max_inflight:
             r = pending[i]
+            folded = try_fold(i, now, not waiting)
+            if folded is not None:
+                slot, idx = folded
+                group = [pending[j] for j in idx]
+                for j in reversed(idx):
+                    del pending[j]
+                start = clock() - t0
+                inflight.append((group, slot, submit(slot, group), start))
+                progressed = True
+                continue
             try:
                 slot = pools.acquire(r.key, now, need_bytes(r.key) if need_bytes else None, allow_new=not waiting)
             except AdmissionError:
@@ -190,14 +228,15 @@ def run_stream(requests, pools: PlanPools, submit, poll, clock=time.perf_counter
                 continue
             del pending[i]
             start = clock() - t0
-            inflight.append((r, slot, submit(slot, r), start))
+            inflight.append(([r], slot, submit(slot, [r]), start))
             progressed = True
         still = []
         for item in inflight:
-            r, slot, tok, start = item
+            group, slot, tok, start = item
             if poll(tok):
                 fin = clock() - t0
-                done.append(Done(r.rid, r.arrival, start, fin))
+                for r in group:
+                    done.append(Done(r.rid, r.arrival, start, fin))
                 pools.release(slot, fin)
                 progressed = True
             else:
@@ -222,14 +261,43 @@ def summarize(done, n_points_of) -> dict:
             "span_s": t_last - t_first}
 
 
+class _MultiPlan:
+    """k copies of one problem in one multi-problem plan (lgf_plan_create_multi):
+    one launch per phase solves all of them, each to the result it has alone."""
+
+    def __init__(self, lgfm, p, k, precision, opts):
+        self.lgfm = lgfm
+        self.plan = lgfm.lgf_plan_create_multi([p.blocks] * k, p.n_b, [p.n_levels] * k, p.order, precision, **opts)
+
+    def __call__(self, f, u, stream=None):
+        self.lgfm.lgf_solve(self.plan, f, u, stream)
+        return u
+
+    def workspace_bytes(self):
+        return self.lgfm.lgf_plan_workspace_bytes(self.plan)
+
+    def close(self):
+        if self.plan:
+            self.lgfm.lgf_destroy(self.plan)
+            self.plan = None
+
+
 class GpuServer:
     """The CUDA side: plans per shape, device buffers, pinned host buffers and
     a pool of streams.  problems maps a shape key to a workloads-style problem
     (blocks, n_b, n_levels, order, f); source(request) optionally gives the
-    request's own pinned host source (default: the shape's f)."""
+    request's own pinned host source (default: the shape's f).
+
+    Folding: up to fold_max requests of one shape pending together (shapes of
+    at most fold_points points) run as one multi-problem plan of key (shape,
+    k).  k is limited so that the folded plan picks the same product-kernel
+    form at every level as the plan of one request (the persistent form is
+    chosen per level by its number of sibling groups, 48 or more), so every
+    folded result has the bits of the same request solved alone."""
 
     def __init__(self, precision: int, problems: dict, budget_bytes: float = 120e9, n_streams: int = 16,
-                 tuned_options=None, source=None, keep_results: bool = False, background_plans: bool = True):
+                 tuned_options=None, source=None, keep_results: bool = False, background_plans: bool = True,
+                 fold_max: int = 8, fold_points: int = 1 << 18):
         import concurrent.futures
 
         import torch
@@ -249,13 +317,25 @@ class GpuServer:
         self.keep_results = keep_results
         self.results = {}
         self.largest = {}                   # n_b -> (points, bytes) of the largest plan made
+        self.groups = {}                    # shape -> sibling groups per level of its one-request plan
+        self.fold_max = fold_max
+        self.fold_points = fold_points
+        self.folded = 0                     # requests served in folded plans
         self.device = torch.cuda.current_device()
         self.executor = concurrent.futures.ThreadPoolExecutor(1) if background_plans else None
         self.pools = PlanPools(self._make, self._drop, budget_bytes, executor=self.executor)
 
+    @staticmethod
+    def _split(key):
+        """(shape, copies) of a pool key: a shape, or (shape, k) for a folded plan."""
+        if isinstance(key, tuple) and len(key) == 2 and isinstance(key[1], int) and isinstance(key[0], tuple):
+            return key[0], key[1]
+        return key, 1
+
     def points(self, key) -> int:
-        p = self.problems[key]
-        return len(p.blocks) * p.n_b ** 3
+        shape, k = self._split(key)
+        p = self.problems[shape]
+        return k * len(p.blocks) * p.n_b ** 3
 
     def need_bytes(self, key):
         """Size of a new plan of this shape: measured before for the shape, else
@@ -263,20 +343,35 @@ class GpuServer:
         margin; small plans carry more per-point overhead), else unknown."""
         if key in self.pools.known:
             return self.pools.known[key]
-        big = self.largest.get(self.problems[key].n_b)
+        big = self.largest.get(self.problems[self._split(key)[0]].n_b)
         return None if big is None else 1.25 * big[1] * self.points(key) / big[0]
+
+    def fold(self, shape) -> int:
+        """Largest number of pending requests of this shape to solve together."""
+        if self.fold_max < 2 or shape not in self.groups or self.points(shape) > self.fold_points:
+            return 1
+        k = 1
+        while 2 * k <= self.fold_max and all((g >= 48) == (2 * k * g >= 48) for g in self.groups[shape]):
+            k *= 2
+        return k
 
     def _make(self, key):
         self.torch.cuda.set_device(self.device)     # also on the plan-making thread
-        p = self.problems[key]
-        opts = self.tuned.get(key, {})
-        s = self.lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, self.precision, **opts)
-        shape = (len(p.blocks), p.n_b, p.n_b, p.n_b)
-        f = self.torch.empty(shape, dtype=self.dtype, device="cuda")
+        shape, k = self._split(key)
+        p = self.problems[shape]
+        opts = self.tuned.get(shape, {})
+        if k == 1:
+            s = self.lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, self.precision, **opts)
+            st = s.stats()
+            self.groups[shape] = [g for g in st["groups"][: st["top_product_level"] + 1]]
+        else:
+            s = _MultiPlan(self.lgfm, p, k, self.precision, opts)
+        dims = (k * len(p.blocks), p.n_b, p.n_b, p.n_b)
+        f = self.torch.empty(dims, dtype=self.dtype, device="cuda")
         u = self.torch.empty_like(f)
-        uh = self.torch.empty(shape, dtype=self.dtype).pin_memory()
+        uh = self.torch.empty(dims, dtype=self.dtype).pin_memory()
         nbytes = s.workspace_bytes() + 2 * f.numel() * f.element_size()
-        if self.points(key) > self.largest.get(p.n_b, (0, 0))[0]:
+        if k == 1 and self.points(key) > self.largest.get(p.n_b, (0, 0))[0]:
             self.largest[p.n_b] = (self.points(key), nbytes)
         return (s, f, u, uh), nbytes
 
@@ -286,37 +381,50 @@ class GpuServer:
         s, f, u, uh = handle
         s.close()
 
-    def submit(self, slot, req):
+    def submit(self, slot, reqs):
         s, f, u, uh = slot.handle
         st = self.streams[self.next_stream]
         self.next_stream = (self.next_stream + 1) % len(self.streams)
-        src = self.source(req) if self.source else self.host_f[req.key]
+        nb = f.shape[0] // len(reqs)
         with self.torch.cuda.stream(st):
-            f.copy_(src, non_blocking=True)
+            for i, req in enumerate(reqs):
+                src = self.source(req) if self.source else self.host_f[req.key]
+                f[i * nb:(i + 1) * nb].copy_(src, non_blocking=True)
             s(f, u, st)
             uh.copy_(u, non_blocking=True)
             ev = self.torch.cuda.Event()
             ev.record(st)
-        return (ev, uh, req.rid)
+        if len(reqs) > 1:
+            self.folded += len(reqs)
+        return (ev, uh, [r.rid for r in reqs], nb)
 
     def poll(self, tok):
         if not tok[0].query():
             return False
         if self.keep_results:
-            self.results[tok[2]] = tok[1].numpy().copy()
+            ev, uh, rids, nb = tok
+            for i, rid in enumerate(rids):
+                self.results[rid] = uh[i * nb:(i + 1) * nb].numpy().copy()
         return True
 
     def warm(self, keys):
         """One resident plan per shape, made before the stream starts (largest
         first; each plan's size is measured, not estimated)."""
         keys = sorted(keys, key=self.points, reverse=True)
-        slots = [self.pools.acquire(k, 0.0) for k in keys]
+        slots = []
+        for k in keys:
+            sl = self.pools.acquire(k, 0.0)
+            while sl is None and k in self.pools.making:
+                time.sleep(1e-3)
+                sl = self.pools.acquire(k, 0.0)
+            slots.append(sl)
         for sl in slots:
             if sl is not None:
                 self.pools.release(sl, 0.0)
 
     def run(self, requests, **kw):
-        return run_stream(requests, self.pools, self.submit, self.poll, need_bytes=self.need_bytes, **kw)
+        return run_stream(requests, self.pools, self.submit, self.poll, need_bytes=self.need_bytes,
+                          fold=self.fold, **kw)
 
     def close(self):
         self.torch.cuda.synchronize()

@@ -27,7 +27,7 @@ def test_tuned_options_solve_the_same_problem(tmp_path, monkeypatch):
     cache = json.loads((tmp_path / "tune.json").read_text())
     (entry,) = cache.values()
     assert entry["options"] == opts and len(entry["all"]) >= 8
-    assert entry["ms"] == min(t["ms"] for t in entry["all"])
+    assert entry["ms"] <= min(t["ms"] for t in entry["all"]) / 0.98   # kept unless beaten by 2%
     assert autotune.tune(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32) == opts   # from the cache
     s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32, **opts)
     u = s(torch.from_numpy(p.f).float().cuda())

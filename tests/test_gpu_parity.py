@@ -164,7 +164,7 @@ _variant_problem = None
 
 
 @pytest.mark.parametrize("S", [33, 34, 36])
-@pytest.mark.parametrize("near,interval,separate", [(1, 1, 1), (2, 2, 1), (2, 1, 1), (1, 2, 1), (2, 3, 1),
+@pytest.mark.parametrize("near,interval,separate", [(0, 1, 1), (0, 3, 1), (0, 0, 1),
                                                     (0, 0, 0), (0, 3, 0), (0, 1, 0), (0, 4, 1),
                                                     (0, 5, 0), (0, 5, 1)])
 def test_kernel_variants_and_fft_lengths(S, near, interval, separate):

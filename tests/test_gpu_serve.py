@@ -54,6 +54,37 @@ def test_each_result_same_alone_and_in_the_mix(prec):
         assert np.array_equal(srv.results[r.rid], alone), r.rid
 
 
+@pytest.mark.parametrize("prec", [lgfm.LGF_FP32, lgfm.LGF_FP64])
+def test_folded_requests_same_as_alone(prec):
+    # requests of two small shapes all pending at once: the server folds up to
+    # eight of a shape into one multi-problem plan; each result keeps the bits
+    # of the same request solved alone
+    shapes = [(8, 2), (8, 3)]
+    problems = {k: W.request_problem(k[0], k[1], seed=i) for i, k in enumerate(shapes)}
+    reqs = [Request(i, 0.0, shapes[i % 2], 0) for i in range(32)]
+    dt = torch.float64 if prec == lgfm.LGF_FP64 else torch.float32
+    src = {r.rid: torch.from_numpy(np.random.default_rng(300 + r.rid).uniform(
+        -1.0, 1.0, size=problems[r.key].f.shape)).to(dt).pin_memory() for r in reqs}
+    srv = GpuServer(prec, problems, budget_bytes=8e9, n_streams=4, source=lambda r: src[r.rid % 100],
+                    keep_results=True)
+    srv.warm(shapes)
+    assert srv.fold(shapes[0]) == 8
+    done, rejected = srv.run(reqs)
+    # a second round finds the folded plans made during the first
+    done2, _ = srv.run([Request(100 + r.rid, 0.0, r.key, 0) for r in reqs])
+    srv.close()
+    assert not rejected and len(done) == 32 and len(done2) == 32
+    assert srv.folded >= 16
+    for r in reqs:
+        p = problems[r.key]
+        s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, prec)
+        alone = s(src[r.rid].cuda()).cpu().numpy()
+        torch.cuda.synchronize()
+        s.close()
+        assert np.array_equal(srv.results[r.rid], alone), r.rid
+        assert np.array_equal(srv.results[100 + r.rid], alone), r.rid
+
+
 def test_budget_too_small_rejects():
     problems = {(16, 4): W.request_problem(16, 4, seed=0)}
     srv = GpuServer(lgfm.LGF_FP32, problems, budget_bytes=1e6, n_streams=2)

@@ -38,10 +38,11 @@ class Sim:
     def drop(self, h):
         self.used -= self.live.pop(h)
 
-    def submit(self, slot, req):
+    def submit(self, slot, reqs):
         self.running += 1
         self.max_running = max(self.max_running, self.running)
-        return [self.t + self.service[req.key], False]
+        key = reqs[0].key
+        return [self.t + self.service[key[0] if isinstance(key, tuple) else key], False]
 
     def poll(self, tok):
         if self.t >= tok[0] and not tok[1]:
@@ -178,3 +179,26 @@ def test_plan_made_in_the_background_does_not_block_others():
     # every fast request finished before the slow one could start
     assert all(d[i].finish <= d[0].start for i in range(1, 11))
     assert sim.made == 2
+
+
+def test_requests_pending_together_are_folded():
+    # eight requests of one shape arrive at once: with fold allowing 4, they
+    # run as two folded plans of 4 (key ("a", 4)), each completing all four
+    sizes = {"a": 10, ("a", 4): 30, ("a", 2): 18}
+    sim = Sim(sizes, {"a": 1e-3})
+    pools = PlanPools(sim.make, sim.drop, budget_bytes=100)
+    submitted = []
+
+    def submit(slot, reqs):
+        submitted.append((slot.key, [r.rid for r in reqs]))
+        return sim.submit(slot, reqs)
+
+    reqs = [Request(i, 0.0, "a", 1) for i in range(8)] + [Request(8, 0.5, "a", 1)]
+    done, rejected = run_stream(reqs, pools, submit, sim.poll, clock=sim.clock, sleep=sim.sleep,
+                                need_bytes=lambda k: sizes[k], fold=lambda key: 4)
+    assert not rejected and sorted(d.rid for d in done) == list(range(9))
+    assert [k for k, _ in submitted[:2]] == [("a", 4), ("a", 4)]
+    assert sorted(r for _, rids in submitted[:2] for r in rids) == list(range(8))
+    assert submitted[-1] == ("a", [8])             # alone: nothing pending beside it
+    d = {x.rid: x for x in done}
+    assert len({d[i].finish for i in range(4)}) == 1   # a folded group completes together
