@@ -119,12 +119,20 @@ __global__ void __launch_bounds__(fft_threads<T, S, NIN>(), fft_min_blocks<T, S,
     constexpr size_t ITEM = fft_item_smem<T, S, NIN>();
     constexpr bool DIRECT = fft_direct_rows<T, NIN>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ R2CItem its[K];
     const int first = blockIdx.x * K;
     const int nk = min(K, n_items - first);   // items of this CTA
+    // one item: its indices in registers; several: in shared memory
+    const R2CItem it0 = items[first];
+    if constexpr (K > 1) {
+        if (threadIdx.x < nk) its[threadIdx.x] = items[first + threadIdx.x];
+        __syncthreads();
+    }
+    auto item = [&](int b) { return K == 1 ? it0 : its[b]; };
     // item b's partially transformed cube and staged input
     auto Bof = [&](int b) { return reinterpret_cast<cx<T>*>(smem_raw + b * ITEM); };
     auto Xof = [&](int b) { return reinterpret_cast<T*>(Bof(b) + NIN * PP); };
-    auto in_of = [&](int b) { return src + int64_t(items[first + b].src) * src_stride; };
+    auto in_of = [&](int b) { return src + int64_t(item(b).src) * src_stride; };
     // a kernel launched after this one with programmatic serialization (the
     // level-0 products) may start its prologue once every CTA got here; it
     // waits for this grid to finish before it reads the spectra
@@ -139,8 +147,8 @@ __global__ void __launch_bounds__(fft_threads<T, S, NIN>(), fft_min_blocks<T, S,
     }
     // x pass: lines l and l + NP (rows of the (y, z) plane) as one complex transform
     constexpr int NL = NIN * NIN, NP = (NL + 1) / 2;
-    for (int p = threadIdx.x; p < nk * NP; p += blockDim.x) {
-        const int b = p / NP, l0 = p % NP, l1 = l0 + NP;
+    for (int p = threadIdx.x; p < (K == 1 ? NP : nk * NP); p += blockDim.x) {
+        const int b = K == 1 ? 0 : p / NP, l0 = K == 1 ? p : p % NP, l1 = l0 + NP;
         const bool has1 = l1 < NL;
         cx<T>* B = Bof(b);
         cx<T> z[S];
@@ -190,8 +198,8 @@ __global__ void __launch_bounds__(fft_threads<T, S, NIN>(), fft_min_blocks<T, S,
     }
     __syncthreads();
     // y pass: lines (kx, z), in place within the column
-    for (int q = threadIdx.x; q < nk * NX * NIN; q += blockDim.x) {
-        const int b = q / (NX * NIN), l = q % (NX * NIN);
+    for (int q = threadIdx.x; q < (K == 1 ? NX * NIN : nk * NX * NIN); q += blockDim.x) {
+        const int b = K == 1 ? 0 : q / (NX * NIN), l = K == 1 ? q : q % (NX * NIN);
         const int kx = l % NX, zz = l / NX;
         cx<T>* col = Bof(b) + zz * PP + kx;
         cx<T> v[S];
@@ -203,11 +211,11 @@ __global__ void __launch_bounds__(fft_threads<T, S, NIN>(), fft_min_blocks<T, S,
     }
     __syncthreads();
     // z pass: lines (kx, ky), results to global (coalesced across the CTA)
-    for (int q = threadIdx.x; q < nk * NX * S; q += blockDim.x) {
-        const int b = q / (NX * S), l = q % (NX * S);
+    for (int q = threadIdx.x; q < (K == 1 ? NX * S : nk * NX * S); q += blockDim.x) {
+        const int b = K == 1 ? 0 : q / (NX * S), l = K == 1 ? q : q % (NX * S);
         const int kx = l % NX, ky = l / NX;
         const cx<T>* col = Bof(b) + ky * NXP + kx;
-        cx<T>* out = spec + int64_t(items[first + b].dst) * NWS;
+        cx<T>* out = spec + int64_t(item(b).dst) * NWS;
         cx<T> v[S];
 #pragma unroll
         for (int zz = 0; zz < S; ++zz) v[zz] = zz < NIN ? col[zz * PP] : czero<T>();
@@ -234,21 +242,29 @@ __global__ void __launch_bounds__(fft_threads<T, S, NOUT>(), fft_min_blocks<T, S
     constexpr size_t ITEM = fft_item_smem<T, S, NOUT>();
     constexpr bool DIRECT = fft_direct_rows<T, NOUT>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ C2RItem its[K];
     const int first = blockIdx.x * K;
     const int nk = min(K, n_items - first);   // items of this CTA
+    // one item: its indices in registers; several: in shared memory
+    const C2RItem it0 = items[first];
+    if constexpr (K > 1) {
+        if (threadIdx.x < nk) its[threadIdx.x] = items[first + threadIdx.x];
+        __syncthreads();
+    }
+    auto item = [&](int b) { return K == 1 ? it0 : its[b]; };
     auto Bof = [&](int b) { return reinterpret_cast<cx<T>*>(smem_raw + b * ITEM); };
     auto Oof = [&](int b) { return reinterpret_cast<T*>(Bof(b) + NOUT * PP); };
-    auto out_of = [&](int b) { return dst + int64_t(items[first + b].dst) * dst_stride; };
+    auto out_of = [&](int b) { return dst + int64_t(item(b).dst) * dst_stride; };
     auto add_of = [&](int b) -> const T* {
-        const int aux = items[first + b].aux;
+        const int aux = item(b).aux;
         return (add != nullptr && aux >= 0) ? add + int64_t(aux) * add_stride : nullptr;
     };
 
     // z pass: lines (kx, ky); keep z < NOUT
-    for (int q = threadIdx.x; q < nk * NX * S; q += blockDim.x) {
-        const int b = q / (NX * S), l = q % (NX * S);
+    for (int q = threadIdx.x; q < (K == 1 ? NX * S : nk * NX * S); q += blockDim.x) {
+        const int b = K == 1 ? 0 : q / (NX * S), l = K == 1 ? q : q % (NX * S);
         const int kx = l % NX, ky = l / NX;
-        const cx<T>* in = spec + int64_t(items[first + b].src) * NWS;
+        const cx<T>* in = spec + int64_t(item(b).src) * NWS;
         cx<T> v[S];
 #pragma unroll
         for (int kz = 0; kz < S; ++kz) v[kz] = ldg_cx(in + int64_t(kz) * S * NX + l);
@@ -259,8 +275,8 @@ __global__ void __launch_bounds__(fft_threads<T, S, NOUT>(), fft_min_blocks<T, S
     }
     __syncthreads();
     // y pass: lines (kx, z < NOUT); keep y < NOUT
-    for (int q = threadIdx.x; q < nk * NX * NOUT; q += blockDim.x) {
-        const int b = q / (NX * NOUT), l = q % (NX * NOUT);
+    for (int q = threadIdx.x; q < (K == 1 ? NX * NOUT : nk * NX * NOUT); q += blockDim.x) {
+        const int b = K == 1 ? 0 : q / (NX * NOUT), l = K == 1 ? q : q % (NX * NOUT);
         const int kx = l % NX, zz = l / NX;
         cx<T>* col = Bof(b) + zz * PP + kx;
         cx<T> v[S];
@@ -273,8 +289,8 @@ __global__ void __launch_bounds__(fft_threads<T, S, NOUT>(), fft_min_blocks<T, S
     __syncthreads();
     // x pass: two Hermitian half-lines (rows l and l + NP) per complex inverse
     constexpr int NL = NOUT * NOUT, NP = (NL + 1) / 2;
-    for (int p = threadIdx.x; p < nk * NP; p += blockDim.x) {
-        const int b = p / NP, l0 = p % NP, l1 = l0 + NP;
+    for (int p = threadIdx.x; p < (K == 1 ? NP : nk * NP); p += blockDim.x) {
+        const int b = K == 1 ? 0 : p / NP, l0 = K == 1 ? p : p % NP, l1 = l0 + NP;
         const bool has1 = l1 < NL;
         const cx<T>* B = Bof(b);
         const int y0 = l0 % NOUT, z0 = l0 / NOUT, y1 = l1 % NOUT, z1 = l1 / NOUT;
