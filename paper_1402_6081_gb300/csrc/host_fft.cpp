@@ -2,7 +2,7 @@
 // Recursive mixed-radix decimation in time: a length n = r * m transform is r
 // transforms of length m on the stride-r subsequences, combined with twiddles
 // W_n^{j k1} and a radix-r DFT; r is the smallest prime factor of n.  Roots of
-// unity come from one table per call (lengths up to 64).
+// unity come from one table per call (lengths up to 96).
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -13,7 +13,7 @@ namespace lgf {
 namespace {
 
 using cd = std::complex<double>;
-constexpr int kMaxN = 64;
+constexpr int kMaxN = 96;
 
 int smallest_factor(int n) {
     if (n % 2 == 0) return 2;

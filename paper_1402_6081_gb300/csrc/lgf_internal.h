@@ -27,7 +27,7 @@ std::shared_ptr<const std::vector<double>> green_abs_table(int h, int V);
 // In-place complex DFT of length n with sign -1 (forward) or +1 (inverse,
 // unnormalised), on a strided sequence.
 void fft_inplace(std::complex<double>* x, int n, int stride, int sign);
-// count lines at base + c*line_stride, each n elements at stride (n <= 64).
+// count lines at base + c*line_stride, each n elements at stride (n <= 96).
 void fft_lines(std::complex<double>* base, int n, int stride, int count, int64_t line_stride,
                int sign);
 
@@ -174,6 +174,30 @@ struct LaunchExt {
 };
 // Transform lengths the persistent products kernel is built for (FP32)
 bool persist_supported(int S);
+
+// The steps of a solve with every size a run-time argument (generic.cu), for
+// the block sizes without per-size kernels (even n_b of [18, 32]).  The
+// transforms pass between the level's spectrum buffer (slot layout) and a
+// scratch of n_items x n x S x (S/2 + 1) complex values (n = n_in or n_out),
+// with a twiddle table (cos, sin)(2 pi m / S), m < S, in the plan precision;
+// Reg and Interp use the 1D matrices W (2 x n_I x n_I, device memory) and a
+// scratch of n_ctas x 3 n_I^3 values.
+template <typename T>
+struct Generic {
+    static cudaError_t r2c(int S, int n_in, const T* src, int64_t src_stride, const R2CItem* items, int n_items,
+                           void* spec, void* scratch, const void* twt, cudaStream_t st);
+    static cudaError_t c2r(int S, int n_out, const void* spec, const C2RItem* items, int n_items, void* scratch,
+                           T* dst, int64_t dst_stride, const T* add, int add_n, int64_t add_stride, const void* twt,
+                           cudaStream_t st);
+    static cudaError_t mac(const void* fh, const void* kh, void* uh, const int* gnbr, int n_groups, int S,
+                           int include_self, cudaStream_t st);
+    static cudaError_t reg(int n_b, const T* child_src, int child_is_block, const int* child_index,
+                           const int* parent_slot, int n_parents, T* dst, const T* W_dev, int comp, T* scratch,
+                           int n_ctas, cudaStream_t st);
+    static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items, T* u, const T* up,
+                              const T* W_dev, int accumulate, const int* block, int comp, T* scratch, int n_ctas,
+                              cudaStream_t st);
+};
 
 // Level-0 transforms as persistent kernels, FP32 (kernels_f32.cu): one CTA
 // per SM (grid from cube_fft_grid, which also sets the kernels' shared-memory

@@ -54,7 +54,8 @@ int s_interval(int n_b) {
         case 10: return 24;
         case 12: return 28;
         case 14: return 32;
-        default: return 33;
+        case 16: return 33;
+        default: return 2 * n_b + 2;   // the run-time-size kernels (n_b 18..32)
     }
 }
 static bool s_interval_supported(int n_b, int S) {
@@ -62,8 +63,9 @@ static bool s_interval_supported(int n_b, int S) {
     if (n_b == 16) return S == 33 || S == 34 || S == 36;
     return S == s_interval(n_b);
 }
-// block sizes with built kernels: the even sizes 4..16
-static bool n_b_supported(int n_b) { return n_b >= 4 && n_b <= 16 && n_b % 2 == 0; }
+// block sizes with per-size kernels (the even sizes 4..16); the other even
+// sizes up to 32 run the run-time-size kernels of generic.cu
+static bool n_b_specialized(int n_b) { return n_b >= 4 && n_b <= 16 && n_b % 2 == 0; }
 
 // ---------------------------------------------------------------------------
 // Interpolation stencil (Sec. 2.5): child c node i sits at parent coordinate
@@ -345,6 +347,7 @@ struct Level {
 struct DevLevel {
     int n_groups = 0;
     bool m2l = false;
+    void* gs = nullptr;   // transform scratch of the run-time-size kernels
     void* fh = nullptr;
     void* uh = nullptr;
     void* ft = nullptr;
@@ -394,6 +397,14 @@ struct lgf_plan_s {
     // ([0..1] forward, [2..3] inverse)
     int fft_kernel = 0;
     int symmetric_spectra = 0;          // option: 1 = reflection-reduced interval tables
+    // block sizes without per-size kernels: the run-time-size kernels, their
+    // twiddle tables (per transform length), the stencils in device memory
+    // (per parent level) and the Reg / Interp scratch (n_ctas x 3 n_I^3 each)
+    bool generic = false;
+    std::map<int, void*> tw_dev;
+    std::vector<void*> W_dev;
+    void* gscratch[2] = {nullptr, nullptr};
+    int gctas = 0;
     int mac_gpc = 0;                    // option: sibling groups per CTA of the one-CTA-per-chunk products
     int cube_grid[2] = {0, 0};
     int* fft_ctr = nullptr;
@@ -948,7 +959,7 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             const int kind = l == 0 ? (P->merged ? kBlock : kNear) : kInterval;
             // reflection-reduced tables where the one-CTA-per-chunk products
             // run (the persistent kernel streams the half table by tensor copies)
-            D.oct = P->symmetric_spectra == 1 && kind != kNear && !uses_persist(P, l);
+            D.oct = P->symmetric_spectra == 1 && kind != kNear && !uses_persist(P, l) && !P->generic;
             if ((s = get_spectra(P->device, nb, S, h, kind, P->prec, D.kh, D.oct ? 1 : 0)) != LGF_OK) return s;
             D.pp.tmap = D.kh->has_tmap ? &D.kh->tmap : nullptr;
         }
@@ -1051,6 +1062,63 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             P->W = d;
         }
     }
+    if (P->generic) {
+        lgf_status s;
+        const bool f64 = P->prec == LGF_FP64;
+        // twiddles (cos, sin)(2 pi m / S) of both transform lengths, FP64 values rounded once
+        for (int S : {P->S0, P->SI}) {
+            if (P->tw_dev.count(S)) continue;
+            std::vector<double> t(2 * size_t(S));
+            for (int m = 0; m < S; ++m) {
+                const double a = 2.0 * M_PI * double(m) / double(S);
+                t[2 * size_t(m)] = std::cos(a);
+                t[2 * size_t(m) + 1] = std::sin(a);
+            }
+            void* d = nullptr;
+            if (f64) {
+                double* dd = nullptr;
+                if ((s = upload(P, t, &dd)) != LGF_OK) return s;
+                d = dd;
+            } else {
+                std::vector<float> tf(t.begin(), t.end());
+                float* df = nullptr;
+                if ((s = upload(P, tf, &df)) != LGF_OK) return s;
+                d = df;
+            }
+            P->tw_dev[S] = d;
+        }
+        // the stencils of every parent level in device memory
+        P->W_dev.assign(size_t(L) + 1, nullptr);
+        for (int l = 2; l <= L; ++l) {
+            if (f64) {
+                double* d = nullptr;
+                if ((s = upload(P, P->Wd[size_t(l)], &d)) != LGF_OK) return s;
+                P->W_dev[size_t(l)] = d;
+            } else {
+                float* d = nullptr;
+                if ((s = upload(P, P->Wf[size_t(l)], &d)) != LGF_OK) return s;
+                P->W_dev[size_t(l)] = d;
+            }
+        }
+        // transform scratch of each level: its larger item list, n_I planes
+        for (int l = 0; l <= Lmac; ++l) {
+            DevLevel& D = P->lev[size_t(l)];
+            const int S = l == 0 ? P->S0 : P->SI;
+            const size_t items = size_t(std::max({D.n_r2c, D.n_c2r, l == 0 ? P->n_out : 0}));
+            if ((s = dalloc(P, items * size_t(nI) * size_t(S) * size_t(S / 2 + 1) * 2 * elem, &D.gs, false)) !=
+                LGF_OK)
+                return s;
+        }
+        // Reg / Interp scratch: two CTAs per SM, 3 cubes of n_I^3 each
+        if (Lmac >= 2) {
+            int n_sm = 0;
+            LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
+            P->gctas = 2 * n_sm;
+            const size_t bytes = size_t(P->gctas) * 3 * n3 * elem;
+            for (void*& g : P->gscratch)
+                if ((s = dalloc(P, bytes, &g, false)) != LGF_OK) return s;
+        }
+    }
     return ok();
 }
 
@@ -1087,6 +1155,34 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         if constexpr (sizeof(T) == 8) return reinterpret_cast<const T*>(P->Wd[size_t(l)].data());
         else return reinterpret_cast<const T*>(P->Wf[size_t(l)].data());
     };
+    // Transforms, products, Reg and Interp: the per-size kernels, or for the
+    // block sizes without them the run-time-size kernels (generic.cu), which
+    // pass the transforms through the level's other spectrum buffer.
+    const bool gen = P->generic;
+    using Gn = Generic<T>;
+    auto r2c_of = [&](int S, int n_in, const T* src, int64_t stride, DevLevel& D, cudaStream_t s) {
+        if (gen) return Gn::r2c(S, n_in, src, stride, D.r2c, D.n_r2c, D.fh, D.gs, P->tw_dev.at(S), s);
+        return Lc::r2c(S, n_in, src, stride, D.r2c, D.n_r2c, D.fh, s);
+    };
+    auto c2r_of = [&](int S, int n_out, DevLevel& D, const C2RItem* items, int n, T* dst, int64_t ds, const T* add,
+                      int add_n, int64_t as, cudaStream_t s) {
+        if (gen) return Gn::c2r(S, n_out, D.uh, items, n, D.gs, dst, ds, add, add_n, as, P->tw_dev.at(S), s);
+        return Lc::c2r(S, n_out, D.uh, items, n, dst, ds, add, add_n, as, s);
+    };
+    auto reg_of = [&](int l, int nm, const T* src, int from_blocks, const int* child, const int* parent, int n, T* dst,
+                      const T* W, int comp, cudaStream_t s) {
+        if (gen)
+            return Gn::reg(nb, src, from_blocks, child, parent, n, dst, static_cast<const T*>(P->W_dev[size_t(l)]),
+                           comp, static_cast<T*>(P->gscratch[0]), P->gctas, s);
+        return Lc::reg(nb, nm, src, from_blocks, child, parent, n, dst, W, comp, s);
+    };
+    auto interp_of = [&](int lp, int nm, const int* slot, const int* parent, int n, T* out, const T* up, const T* W,
+                         int accumulate, const int* block, int comp, cudaStream_t s) {
+        if (gen)
+            return Gn::interp(nb, slot, parent, n, out, up, static_cast<const T*>(P->W_dev[size_t(lp)]), accumulate,
+                              block, comp, static_cast<T*>(P->gscratch[1]), P->gctas, s);
+        return Lc::interp(nb, nm, slot, parent, n, out, up, W, accumulate, block, comp, s);
+    };
     cudaError_t e;
     const int Lm = P->Lmac;
     const bool conc = !P->single_stream;
@@ -1107,7 +1203,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             if (P->fft_kernel == 2)
                 return c2r_cube(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, P->cube_grid[1],
                                 P->fft_ctr + 2, P->err, st);
-        return Lc::c2r(P->S0, nb, lev[0].uh, P->out_items, P->n_out, u, b3, add, nI, n3, st);
+        return c2r_of(P->S0, nb, lev[0], P->out_items, P->n_out, u, b3, add, nI, n3, st);
     };
     // fork: the other chains start after all prior work on the caller's stream
     if (conc && (Lm >= 2 || (Lm >= 1 && !P->merged))) {
@@ -1134,11 +1230,11 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
         }
         cudaError_t r = cudaSuccess;
         const int nc = D.n_int_comp;
-        if (nc > 0) r = Lc::interp(nb, nm, D.int_slot, D.int_parent, nc, out, up, W, accumulate, block, 1, s);
+        if (nc > 0) r = interp_of(l + 1, nm, D.int_slot, D.int_parent, nc, out, up, W, accumulate, block, 1, s);
         if (nc > 0 && D.n_int > nc) ++P->launches_last;   // the second launch of this phase
         if (r == cudaSuccess && D.n_int > nc)
-            r = Lc::interp(nb, nm, D.int_slot + nc, D.int_parent + nc, D.n_int - nc, out, up, W, accumulate,
-                           block ? block + nc : nullptr, 0, s);
+            r = interp_of(l + 1, nm, D.int_slot + nc, D.int_parent + nc, D.n_int - nc, out, up, W, accumulate,
+                          block ? block + nc : nullptr, 0, s);
         return r;
     };
     // ---- levels >= 2 upward on s2: Reg from the level below, forward FFT
@@ -1158,18 +1254,18 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                 cudaError_t r = cudaSuccess;
                 const int nc = D.n_reg_comp;
                 if (nc > 0)
-                    r = Lc::reg(nb, nm, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, nc,
-                                static_cast<T*>(D.ft), W, 1, s2);
+                    r = reg_of(l, nm, src, from_blocks ? 1 : 0, D.reg_child, D.reg_parent, nc, static_cast<T*>(D.ft),
+                               W, 1, s2);
                 if (nc > 0 && D.n_reg > nc) ++P->launches_last;
                 if (r == cudaSuccess && D.n_reg > nc)
-                    r = Lc::reg(nb, nm, src, from_blocks ? 1 : 0, D.reg_child + 8 * size_t(nc),
-                                D.reg_parent + nc, D.n_reg - nc, static_cast<T*>(D.ft), W, 0, s2);
+                    r = reg_of(l, nm, src, from_blocks ? 1 : 0, D.reg_child + 8 * size_t(nc), D.reg_parent + nc,
+                               D.n_reg - nc, static_cast<T*>(D.ft), W, 0, s2);
                 return r;
             });
             if (e != cudaSuccess) return cuda_fail(e, "regularization");
             if (D.m2l) {
                 e = timed(P, "r2c_interval", s2, [&] {
-                    return Lc::r2c(P->SI, nI, static_cast<const T*>(D.ft), n3, D.r2c, D.n_r2c, D.fh, s2);
+                    return r2c_of(P->SI, nI, static_cast<const T*>(D.ft), n3, D, s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
             }
@@ -1183,6 +1279,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             if (!D.m2l) continue;
             e = timed(P, "mac_interval_l2plus", s2, [&] {
                 if (uses_persist(P, l)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s2);
+                if (gen) return Gn::mac(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, 0, s2);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
                                         0, table_map(D), P->err, s2, D.oct ? 1 : 0, P->mac_gpc);
             });
@@ -1192,7 +1289,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             DevLevel& D = lev[size_t(l)];
             if (D.m2l) {
                 e = timed(P, "c2r_interval", s2, [&] {
-                    return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s2);
+                    return c2r_of(P->SI, nI, D, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s2);
                 });
                 if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
             } else {
@@ -1224,7 +1321,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                     return r2c_cube(P->S0, nb, P->in_map, lev[0].r2c, lev[0].n_r2c, lev[0].fh, P->cube_grid[0],
                                     P->fft_ctr, P->err, st);
             }
-        return Lc::r2c(P->S0, nb, f, b3, lev[0].r2c, lev[0].n_r2c, lev[0].fh, st);
+        return r2c_of(P->S0, nb, f, b3, lev[0], st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "level-0 forward FFT");
     if (split) LGF_CUDA(wait(st, 1));
@@ -1235,6 +1332,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
             const int early = !split && P->ev.empty() ? 1 : 0;
             if (uses_persist(P, 0))
                 return Lc::mac_persist(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].pp, P->S0, early, st);
+            if (gen) return Gn::mac(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].n_groups, P->S0, 1, st);
             return Lc::mac_interval(lev[0].fh, lev[0].kh->ptr, lev[0].uh, lev[0].gnbr, lev[0].order, lev[0].n_groups,
                                     P->S0, P->interval_kernel == 3 ? 3 : 1, 1, table_map(lev[0]), P->err, st,
                                     lev[0].oct ? 1 : 0, P->mac_gpc);
@@ -1269,16 +1367,17 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     if (Lm >= 1 && !P->merged) {
         DevLevel& D = lev[1];
         if (D.m2l) {
-            e = timed(P, "r2c_interval", s1, [&] { return Lc::r2c(P->SI, nb, f, b3, D.r2c, D.n_r2c, D.fh, s1); });
+            e = timed(P, "r2c_interval", s1, [&] { return r2c_of(P->SI, nb, f, b3, D, s1); });
             if (e != cudaSuccess) return cuda_fail(e, "interval forward FFT");
             e = timed(P, "mac_interval_l1", s1, [&] {
                 if (uses_persist(P, 1)) return Lc::mac_persist(D.fh, D.kh->ptr, D.uh, D.pp, P->SI, 0, s1);
+                if (gen) return Gn::mac(D.fh, D.kh->ptr, D.uh, D.gnbr, D.n_groups, P->SI, 0, s1);
                 return Lc::mac_interval(D.fh, D.kh->ptr, D.uh, D.gnbr, D.order, D.n_groups, P->SI, P->interval_kernel,
                                         0, table_map(D), P->err, s1, D.oct ? 1 : 0, P->mac_gpc);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interaction-list products");
             e = timed(P, "c2r_interval", s1, [&] {
-                return Lc::c2r(P->SI, nI, D.uh, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s1);
+                return c2r_of(P->SI, nI, D, D.c2r, D.n_c2r, static_cast<T*>(D.ut), n3, nullptr, 0, 0, s1);
             });
             if (e != cudaSuccess) return cuda_fail(e, "interval inverse FFT");
         } else {
@@ -1374,9 +1473,6 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     if (n_blocks > (int64_t(1) << 26)) return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: more than 2^26 blocks");
     if (n_b < 4 || n_b > 32 || n_b % 2 != 0)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: n_b must be even, 4 <= n_b <= 32");
-    if (!n_b_supported(n_b))
-        return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: n_b = " + std::to_string(n_b) +
-                                             " is not built (block sizes 4, 6, ..., 16 are)");
     if (interp_order < 0 || interp_order + 1 > n_b + 1)
         return fail(LGF_ERR_INVALID_ARG, "lgf_plan_create: need 0 <= interp_order and interp_order + 1 <= n_b + 1");
     if (precision != LGF_FP32 && precision != LGF_FP64)
@@ -1403,6 +1499,7 @@ static lgf_status create_plan(const int32_t* block_ijk, const int64_t* offsets, 
     P->n_points = n_blocks * int64_t(n_b) * n_b * n_b;
     P->S0 = s_level0(n_b);
     P->SI = s_interval(n_b);
+    P->generic = !n_b_specialized(n_b);
     if (opts && opts->fft_size_interval != 0) {
         if (!s_interval_supported(n_b, opts->fft_size_interval))
             return fail(LGF_ERR_UNSUPPORTED, "lgf_plan_create: fft_size_interval " +

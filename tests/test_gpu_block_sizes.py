@@ -114,13 +114,17 @@ def test_level_orders_against_oracle():
 
 def test_block_size_errors():
     b = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
-    for n_b, status in ((7, 1), (2, 1), (34, 1), (18, 2), (32, 2)):
+    for n_b, status in ((7, 1), (2, 1), (34, 1), (19, 1), (0, 1)):
         with pytest.raises(lgfm.LgfError) as e:
             lgfm.lgf_plan_create(b, n_b, 1, 3, lgfm.LGF_FP32)
         assert e.value.status == status, n_b
+    for n_b in (10, 20):
+        with pytest.raises(lgfm.LgfError) as e:
+            lgfm.lgf_plan_create(b, n_b, 1, 3, lgfm.LGF_FP32, lgfm.LGF_INTERP_BF16)
+        assert e.value.status == 2
     with pytest.raises(lgfm.LgfError) as e:
-        lgfm.lgf_plan_create(b, 10, 1, 3, lgfm.LGF_FP32, lgfm.LGF_INTERP_BF16)
-    assert e.value.status == 2
+        lgfm.Solver(b, 20, 1, 3, lgfm.LGF_FP32, fft_kernel=2)
+    assert e.value.status == 1
     with pytest.raises(lgfm.LgfError) as e:
         lgfm.Solver(b, 8, 1, 3, lgfm.LGF_FP32, level_orders={2: 9})
     assert e.value.status == 1

@@ -195,8 +195,8 @@ def test_plan_errors():
         lgfm.lgf_plan_create(W.full_box_blocks(8), 8, 2, 6, lgfm.LGF_FP32)
     assert e.value.status == 2 and "n_levels >= 3" in str(e.value)
     with pytest.raises(lgfm.LgfError) as e:
-        lgfm.lgf_plan_create(W.full_box_blocks(2), 18, 1, 4, lgfm.LGF_FP32)
-    assert e.value.status == 2
+        lgfm.lgf_plan_create(W.full_box_blocks(2), 34, 1, 4, lgfm.LGF_FP32)
+    assert e.value.status == 1
     with pytest.raises(lgfm.LgfError) as e:
         lgfm.lgf_plan_create(W.full_box_blocks(2), 8, 1, 9, lgfm.LGF_FP32)
     assert e.value.status == 1
