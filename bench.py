@@ -422,13 +422,17 @@ def fft_conv_run(torch, lgfm, steps: int, flush, peak_tf: float):
 def error_sweep_run(torch, lgfm, diameter: int = 128):
     """The paper's error experiment on the GPU (Sec. 4.1): exact manufactured
     solutions on a cube, a sphere and a spherical shell of the same diameter,
-    n_max = 10, n_I = n_b + 1 = 11..17; relative L-infinity error of the FP64
-    form, its fitted power of n_I (the paper: -10.7), and the FP32 / FP64
-    rates.  Also the Sec. 2.5 parameter choice for two targets."""
-    out = {"config": {"workload": "manufactured_sweep", "diameter": diameter, "n_max": 10, "n_I": [11, 13, 15, 17]}}
+    n_max = 10, n_I = n_b + 1 = 11..27; relative L-infinity error of the FP64
+    form, its fitted power of n_I (the paper: -10.7 for n_I = 11..28) over the
+    whole range and over n_I <= 23 (above that the error reaches the FP64
+    rounding floor of these badly conditioned random sources), and the FP32 /
+    FP64 rates.  Also the Sec. 2.5 parameter choice for three targets."""
+    sizes = (10, 12, 14, 16, 18, 20, 22, 24, 26)
+    out = {"config": {"workload": "manufactured_sweep", "diameter": diameter, "n_max": 10,
+                      "n_I": [n + 1 for n in sizes]}}
     for shape in ("box", "sphere", "shell"):
         rows = []
-        for n_b in (10, 12, 14, 16):
+        for n_b in sizes:
             blocks = W.shape_blocks(shape, diameter, n_b)
             L = W.levels_for(int(np.ceil(diameter / n_b)))
             m = W.manufactured(blocks, n_b, L, 9, seed=11)
@@ -450,9 +454,11 @@ def error_sweep_run(torch, lgfm, diameter: int = 128):
                                                         / np.abs(m.u_exact).max())
                 s.close()
             rows.append(row)
-        slope = float(np.polyfit(np.log([r["n_I"] for r in rows]),
-                                 np.log([r["fp64_rel_err_vs_exact"] for r in rows]), 1)[0])
-        out[shape] = {"rows": rows, "fp64_error_slope_vs_n_I": slope}
+        def slope(rs):
+            return float(np.polyfit(np.log([r["n_I"] for r in rs]), np.log([r["fp64_rel_err_vs_exact"] for r in rs]),
+                                    1)[0])
+        out[shape] = {"rows": rows, "fp64_error_slope_vs_n_I": slope(rows),
+                      "fp64_error_slope_n_I_11_23": slope([r for r in rows if r["n_I"] <= 23])}
     sel = {}
     for eps, prec, name in ((1e-5, lgfm.LGF_FP32, "fp32_1e-5"), (1e-9, lgfm.LGF_FP64, "fp64_1e-9"),
                             (1.25e-12, lgfm.LGF_FP64, "fp64_1.25e-12")):

@@ -477,7 +477,7 @@ lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double *W);
  * lgf_select_interp - Step 1: n_max = the largest node count n with
  *   Lambda_n^3 eps_p < eps (tensor-product interpolation in 3D; eps_p the
  *   unit roundoff of the precision, 2^-53 FP64, 2^-24 FP32), n <= 17.
- *   Step 2: the smallest built block size n_b (4, 6, ..., 16; n_I = n_b + 1
+ *   Step 2: the smallest supported block size n_b (4, 6, ..., 32; n_I = n_b + 1
  *   >= n_max) whose interpolation of the field the method interpolates errs
  *   by less than eps relative to the field: the LGF of the nearest sources a
  *   parent interval's interaction list can hold (on the face of the interval
@@ -489,7 +489,7 @@ lgf_status lgf_interp_weights(int32_t n_b, int32_t n_max, double *W);
  *     n_max, n_b   receive the choice (interp_order = n_max - 1)
  *     lebesgue     receives Lambda_{n_max} (may be NULL)
  *     interp_err   receives the step-2 error of the chosen n_b (may be NULL)
- *   LGF_ERR_UNSUPPORTED when no built block size reaches eps; the outputs
+ *   LGF_ERR_UNSUPPORTED when no supported block size reaches eps; the outputs
  *   then hold the largest size tried and its error.
  */
 lgf_status lgf_lebesgue_constant(int32_t n, double *out);

@@ -18,7 +18,7 @@ the interval one interval width away (x = 4 n_b; y, z at the face's corners,
 edge midpoints and centre), known at the parent's nodes (spacing 2) and
 interpolated with the Sec. 2.5 stencil to the nodes of its two children
 (spacing 1); the error is relative to max |G| over those nodes.  The block
-sizes tried are 4, 6, ..., 16 with n_b + 1 >= n_max.
+sizes tried are 4, 6, ..., 32 (the supported range) with n_b + 1 >= n_max.
 
 Pins (tests/test_oracle_select.py): the classical Lebesgue constants of 2..5
 equispaced nodes; the paper's example (FP64, eps = 1.25e-12 allows n_max = 10);
@@ -97,7 +97,7 @@ def select(eps: float, precision: str) -> dict:
     """Both steps: {"n_max", "lebesgue", "n_b", "interp_err", "reached"}."""
     n_max, lam = step1_n_max(eps, precision)
     err, chosen = 0.0, 0
-    for n_b in range(4, 17, 2):
+    for n_b in range(4, 33, 2):
         if n_b + 1 < n_max:
             continue
         err = far_field_interp_error(n_b, n_max)

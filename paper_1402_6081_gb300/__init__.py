@@ -502,7 +502,7 @@ def lgf_lebesgue_constant(n: int) -> float:
 def lgf_select_interp(eps: float, precision: int) -> dict:
     """Sec. 2.5's choice of n_max and n_b for a target error (host).  Returns
     {"n_max", "n_b", "lebesgue", "interp_err", "reached"}; reached is False
-    when no built block size meets eps (the largest one tried is returned)."""
+    when no supported block size (4..32) meets eps (the largest one tried is returned)."""
     nm, nb = ctypes.c_int32(), ctypes.c_int32()
     lam, err = ctypes.c_double(), ctypes.c_double()
     st = library().lgf_select_interp(eps, precision, ctypes.byref(nm), ctypes.byref(nb), ctypes.byref(lam),

@@ -15,8 +15,8 @@
 // sources: at a parent interval P' (nodes 2j, j = 0..n_b, spacing 2) the
 // field of the nearest sources its interaction list can hold, on the face
 // of the interval one interval width away (x = 4 n_b, y and z at the face's
-// corners, edge midpoints and centre).  Each candidate n_b (the built sizes,
-// ascending, with n_I >= n_max) interpolates G(x - y) from P''s nodes to the
+// corners, edge midpoints and centre).  Each candidate n_b (the supported
+// sizes 4..32, ascending, with n_I >= n_max) interpolates G(x - y) from P''s nodes to the
 // nodes of its two children (spacing 1) with the Sec. 2.5 stencil, and the
 // first whose maximum error relative to max |G| on the children's nodes is
 // below eps is chosen.
@@ -179,11 +179,11 @@ extern "C" lgf_status lgf_select_interp(double eps, int32_t precision, int32_t* 
     }
     *n_max = nm;
     if (lebesgue) *lebesgue = lam;
-    // Step 2: the smallest built block size whose far-field interpolation
+    // Step 2: the smallest supported block size whose far-field interpolation
     // error is below eps
     double err = 0.0;
     int chosen = 0;
-    for (int nb = 4; nb <= 16; nb += 2) {
+    for (int nb = 4; nb <= 32; nb += 2) {
         if (nb + 1 < nm) continue;
         err = far_field_interp_error(nb, nm);
         chosen = nb;
@@ -192,7 +192,7 @@ extern "C" lgf_status lgf_select_interp(double eps, int32_t precision, int32_t* 
     *n_b = chosen;
     if (interp_err) *interp_err = err;
     if (chosen == 0 || err >= eps)
-        return fail(LGF_ERR_UNSUPPORTED, "lgf_select_interp: no built block size (4..16) reaches eps = " +
+        return fail(LGF_ERR_UNSUPPORTED, "lgf_select_interp: no supported block size (4..32) reaches eps = " +
                                              std::to_string(eps) + " with n_max = " + std::to_string(nm) +
                                              " (largest tried: n_b = " + std::to_string(chosen) +
                                              ", error " + std::to_string(err) + ")");

@@ -109,3 +109,30 @@ def test_error_trend_at_n_max_10(shape):
     print(f"n_max 10 {shape}: error ~ n_I^{slope:.2f}")
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
     assert -13.0 < slope < -9.0, slope
+
+
+def test_error_trend_to_n_I_27_box():
+    # The paper's range n_I = 11..28 (Sec. 4.1) with the even block sizes:
+    # n_I = 11..27 at n_max = 10 on a 128^3 box, against the exact answer.
+    # The error falls like n_I^-10 until it meets the FP64 rounding floor of
+    # this random source (kappa ~ 2e3; a few 1e-11), so the slope is fitted
+    # below n_I = 25 and the largest sizes are only required to stay at the
+    # floor.  n_b >= 18 runs the run-time-size kernels.
+    errs, n_is = [], []
+    for n_b in (10, 14, 18, 22, 26):
+        blocks = W.shape_blocks("box", 128, n_b)
+        L = W.levels_for(int(np.ceil(128 / n_b)))
+        m = W.manufactured(blocks, n_b, L, 9, seed=11)
+        u64, r64 = _solve(m, lgfm.LGF_FP64)
+        e64 = fmm.rel_linf(u64, m.u_exact)
+        record_error(f"sweep10_box128_nI{n_b + 1}", fp64_vs_exact=e64, points=m.n_points, fp64_points_per_s=r64,
+                     levels=L)
+        print(f"n_max 10 box 128 n_I {n_b + 1} (L {L}): fp64 err {e64:.3e}")
+        errs.append(e64)
+        n_is.append(n_b + 1)
+    slope = float(np.polyfit(np.log(n_is[:4]), np.log(errs[:4]), 1)[0])
+    record_error("sweep10_box128_slope_nI_11_23", slope=slope)
+    print(f"n_max 10 box 128: error ~ n_I^{slope:.2f} (n_I 11..23)")
+    assert all(a > b for a, b in zip(errs[:4], errs[1:4])), errs
+    assert -13.0 < slope < -9.0, slope
+    assert errs[-1] < 1e-10, errs
