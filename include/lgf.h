@@ -64,7 +64,9 @@ typedef enum { LGF_FP64 = 0, LGF_FP32 = 1 } lgf_precision;
  * field carries three or more interpolated levels whose FP32 roundings,
  * amplified by the stencil's Lebesgue constant (Sec. 2.5), approach the 1e-5
  * relative tolerance (5-level 512^3 domain: 1.04e-5 plain, 7.7e-6
- * compensated, measured against the FP64 form).  PLAIN forces plain sums in
+ * compensated, measured against the FP64 form); for n_b >= 18 it does so
+ * from level 2 on (three-level irregular tori, n_b = 18: 1.05e-5 plain,
+ * 7.9e-6 compensated).  PLAIN forces plain sums in
  * the plan precision at any depth.  The others
  * (FP32 plans only) run each axis pass as a tensor-core GEMM (tcgen05.mma)
  * with FP32 accumulation; the field between passes stays FP32 and only the

@@ -181,7 +181,8 @@ bool persist_supported(int S);
 // scratch of n_items x n x S x (S/2 + 1) complex values (n = n_in or n_out),
 // with a twiddle table (cos, sin)(2 pi m / S), m < S, in the plan precision;
 // Reg and Interp use the 1D matrices W (2 x n_I x n_I, device memory) and a
-// scratch of n_ctas x 3 n_I^3 values.
+// scratch of n_ctas x 2 n_I^3 values; Reg also 8 n_parents n_I^3 values of
+// slices (one per child).
 template <typename T>
 struct Generic {
     static cudaError_t r2c(int S, int n_in, const T* src, int64_t src_stride, const R2CItem* items, int n_items,
@@ -193,7 +194,7 @@ struct Generic {
                            int include_self, cudaStream_t st);
     static cudaError_t reg(int n_b, const T* child_src, int child_is_block, const int* child_index,
                            const int* parent_slot, int n_parents, T* dst, const T* W_dev, int comp, T* scratch,
-                           int n_ctas, cudaStream_t st);
+                           T* slices, int n_ctas, cudaStream_t st);
     static cudaError_t interp(int n_b, const int* slot, const int* parent, int n_items, T* u, const T* up,
                               const T* W_dev, int accumulate, const int* block, int comp, T* scratch, int n_ctas,
                               cudaStream_t st);

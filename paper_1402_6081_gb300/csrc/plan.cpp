@@ -404,6 +404,7 @@ struct lgf_plan_s {
     std::map<int, void*> tw_dev;
     std::vector<void*> W_dev;
     void* gscratch[2] = {nullptr, nullptr};
+    void* gslices = nullptr;   // Reg's per-child cubes (run-time-size kernels)
     int gctas = 0;
     int mac_gpc = 0;                    // option: sibling groups per CTA of the one-CTA-per-chunk products
     int cube_grid[2] = {0, 0};
@@ -894,12 +895,18 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
     // domain against the FP64 form: plain sums 1.04e-5, compensated 7.7e-6
     // (the 1e-5 FP32 tolerance), for 8% of the solve time; with products at
     // two levels only (the 128^3 torus) the transforms and products dominate
-    // the error and the plain sums are kept.
+    // the error and the plain sums are kept, except for the block sizes of
+    // the run-time-size kernels (n_b >= 18), whose interpolated fields are
+    // summed from more terms: there the sums are compensated from the first
+    // interpolated level on (measured, irregular three-level tori against
+    // FP64: n_b = 18 plain 1.05e-5, compensated 7.9e-6; n_b = 20 1.17e-5 /
+    // 9.7e-6; 2-6% of the solve time).
     std::vector<int> pcomp(np, 0);
     P->comp_sums = 0;
     for (size_t p = 0; p < np; ++p) {
         pcomp[p] = P->interp_mode == LGF_INTERP_COMPENSATED ||
-                   (P->interp_mode == LGF_INTERP_NATIVE && P->prec == LGF_FP32 && hp[p].Lmac >= 3);
+                   (P->interp_mode == LGF_INTERP_NATIVE && P->prec == LGF_FP32 &&
+                    (hp[p].Lmac >= 3 || (P->generic && hp[p].Lmac >= 2)));
         P->comp_sums += pcomp[p];
     }
     P->lev.resize(size_t(Lmac) + 1);
@@ -1109,14 +1116,18 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
                 LGF_OK)
                 return s;
         }
-        // Reg / Interp scratch: two CTAs per SM, 3 cubes of n_I^3 each
+        // Reg / Interp scratch: two CTAs per SM, 2 cubes of n_I^3 each, and
+        // Reg's slices for the largest level (8 per parent)
         if (Lmac >= 2) {
             int n_sm = 0;
             LGF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device));
             P->gctas = 2 * n_sm;
-            const size_t bytes = size_t(P->gctas) * 3 * n3 * elem;
+            const size_t bytes = size_t(P->gctas) * 2 * n3 * elem;
             for (void*& g : P->gscratch)
                 if ((s = dalloc(P, bytes, &g, false)) != LGF_OK) return s;
+            size_t parents = 0;
+            for (int l = 2; l <= Lmac; ++l) parents = std::max(parents, size_t(P->lev[size_t(l)].n_reg));
+            if ((s = dalloc(P, parents * 8 * n3 * elem, &P->gslices, false)) != LGF_OK) return s;
         }
     }
     return ok();
@@ -1173,7 +1184,7 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
                       const T* W, int comp, cudaStream_t s) {
         if (gen)
             return Gn::reg(nb, src, from_blocks, child, parent, n, dst, static_cast<const T*>(P->W_dev[size_t(l)]),
-                           comp, static_cast<T*>(P->gscratch[0]), P->gctas, s);
+                           comp, static_cast<T*>(P->gscratch[0]), static_cast<T*>(P->gslices), P->gctas, s);
         return Lc::reg(nb, nm, src, from_blocks, child, parent, n, dst, W, comp, s);
     };
     auto interp_of = [&](int lp, int nm, const int* slot, const int* parent, int n, T* out, const T* up, const T* W,
