@@ -199,6 +199,24 @@ def cpu_oracle_rate(p, spectra=None):
     return p.n_points / dt, dt, max(1, round(dc / dt)), u
 
 
+def direct_sum_rate():
+    """The exact O(N^2) lattice sum (the oracle's C/OpenMP direct sum, all host
+    threads) on the 32^3 two-level workload: one warm-up, median of three."""
+    from oracle import direct
+    p = W.config(0)
+    direct.direct_sum(p.blocks, p.n_b, p.f)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        direct.direct_sum(p.blocks, p.n_b, p.f)
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
+    n = p.n_points
+    return {"value": n / dt, "unit": "points/s", "pairs_per_s": n * n / dt, "seconds": dt,
+            "threads": os.cpu_count(), "kind": "oracle direct sum (exact)",
+            "sample": f"gaussian_box_32: {n} points, {n * n:.3g} pair terms, median of 3 after 1 warm-up"}
+
+
 def reference_sample():
     """Bounded sample of the workload for the CPU arm: the 64^3 window (4^3
     blocks of 16^3, 2 levels) of the 128^3 torus at the same order."""
@@ -765,6 +783,7 @@ def main():
                                "nproc": os.cpu_count(), "cpu_model": cpu_model(),
                                "sample": f"one full oracle FMM solve of the 128^3 torus ({secs:.1f} s, "
                                          "kernel spectra precomputed outside the timing)"}
+        out["cpu_baseline"]["direct_sum"] = direct_sum_rate()
         out["rel_err_fp32_vs_oracle"] = fmm.rel_linf(got, uref)
         out["rel_err_fp64_vs_oracle"] = fmm.rel_linf(u64.double().cpu().numpy(), uref)
     if world == 1 and not args.no_batch:

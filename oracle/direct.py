@@ -70,3 +70,33 @@ def direct_sum(blocks, n_b: int, f, targets=None) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("direct sum: offset outside the G table")
     return u.reshape(np.shape(f)) if targets is None else u
+
+
+def stencil_residual(blocks, n_b: int, u, f) -> float:
+    """max |L u - f| over the interior of the active grid (points whose six
+    neighbours are all active), relative to max |f|: the discrete Poisson
+    equation L u = f (Eq. dpoisson, 7-point Laplacian, unit spacing) that
+    u = G * f solves exactly at every lattice point."""
+    blocks = np.asarray(blocks, dtype=np.int64)
+    lo = blocks.min(axis=0) * n_b - 1
+    hi = (blocks.max(axis=0) + 1) * n_b + 1
+    shape = tuple(int(v) for v in (hi - lo)[::-1])       # (z, y, x) with a one-point margin
+    pts = point_coords(blocks, n_b).astype(np.int64) - lo
+    xs, ys, zs = pts[:, 0], pts[:, 1], pts[:, 2]
+    U = np.zeros(shape)
+    F = np.zeros(shape)
+    active = np.zeros(shape, dtype=bool)
+    U[zs, ys, xs] = np.asarray(u, dtype=np.float64).reshape(-1)
+    F[zs, ys, xs] = np.asarray(f, dtype=np.float64).reshape(-1)
+    active[zs, ys, xs] = True
+    c = (slice(1, -1),) * 3
+    interior = active[c].copy()
+    lap = -6.0 * U[c]
+    for ax in range(3):
+        for d in (0, 2):
+            sl = [slice(1, -1)] * 3
+            sl[ax] = slice(d, shape[ax] - 2 + d)
+            lap = lap + U[tuple(sl)]
+            interior &= active[tuple(sl)]
+    r = np.abs(lap - F[c])[interior]
+    return float(r.max() / np.abs(F).max()) if r.size else 0.0

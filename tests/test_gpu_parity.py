@@ -103,6 +103,25 @@ def test_torus_128_three_levels():
     check(p)
 
 
+def test_stencil_residuals():
+    # The second check of the 128^3 workload: L u = f on the interior of the
+    # active grid (Eq. dpoisson).  With no interpolation (the 32^3 two-level
+    # case) the residual is rounding; at three levels it is the method's
+    # truncation, so the FP64 GPU residual equals the oracle's up to the
+    # rounding of the stencil applied to a 1e-12 relative difference (12 x
+    # 1e-12 x max|u| / max|f|).
+    p = W.config(0)
+    r1 = direct.stencil_residual(p.blocks, p.n_b, gpu_solve(p, lgfm.LGF_FP64), p.f)
+    p = W.config(1)
+    u64 = gpu_solve(p, lgfm.LGF_FP64)
+    r_gpu = direct.stencil_residual(p.blocks, p.n_b, u64, p.f)
+    r_orc = direct.stencil_residual(p.blocks, p.n_b, oracle_u(p), p.f)
+    slack = 12 * TOL64 * np.abs(u64).max() / np.abs(p.f).max()
+    record_error("stencil_residual", gaussian_box_32_fp64=r1, torus_box_128_fp64=r_gpu, torus_box_128_oracle=r_orc)
+    assert r1 < 1e-12
+    assert abs(r_gpu - r_orc) <= slack and r_orc < 1e-6, (r_gpu, r_orc, slack)
+
+
 @pytest.mark.parametrize("n_b", [4, 8, 16])
 def test_single_block_is_fft_convolution(n_b):
     rng = np.random.default_rng(n_b)

@@ -36,3 +36,28 @@ def test_discrete_poisson_on_interior():
     lap = (grid_u[2:, 1:-1, 1:-1] + grid_u[:-2, 1:-1, 1:-1] + grid_u[1:-1, 2:, 1:-1]
            + grid_u[1:-1, :-2, 1:-1] + grid_u[1:-1, 1:-1, 2:] + grid_u[1:-1, 1:-1, :-2] - 6 * c)
     assert np.abs(lap - grid_f[1:-1, 1:-1, 1:-1]).max() < 1e-12
+
+
+def test_stencil_residual_helper():
+    # the residual helper sees the exact solution's residual at roundoff, and a
+    # planted error of 1e-6 at one interior point as 6e-6 (the stencil's centre
+    # weight) relative to max|f| = 1
+    n_b = 6
+    blocks = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=np.int32)
+    rng = np.random.default_rng(1)
+    f = rng.uniform(-1, 1, size=(4, n_b, n_b, n_b))
+    f.flat[0] = 1.0
+    u = direct.direct_sum(blocks, n_b, f)
+    assert direct.stencil_residual(blocks, n_b, u, f) < 1e-12
+    bad = u.copy()
+    bad[0, 3, 3, 3] += 1e-6
+    assert abs(direct.stencil_residual(blocks, n_b, bad, f) - 6e-6) < 1e-9
+    # a corner of the active grid is neither checked nor a neighbour of an
+    # interior point (its neighbours are on the boundary too)
+    bad = u.copy()
+    bad[0, 0, 0, 0] += 1.0
+    assert direct.stencil_residual(blocks, n_b, bad, f) < 1e-12
+    # a boundary point next to the interior is seen through its neighbour
+    bad = u.copy()
+    bad[0, 0, 3, 3] += 1e-6                                      # z = 0 face
+    assert abs(direct.stencil_residual(blocks, n_b, bad, f) - 1e-6) < 1e-9
