@@ -570,6 +570,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the n_max = 10 error sweep")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
+    ap.add_argument("--profile-workload", default=WORKLOAD, choices=[WORKLOAD, "torus_box_144_nb18"],
+                    help="with --profile-only: the workload solved (torus_box_144_nb18: 8^3 blocks of 18^3, "
+                         "3 levels, the run-time-size kernels)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -598,6 +601,8 @@ def main():
     dev = torch.cuda.current_device()
 
     p = W.config(1)
+    if args.profile_only and args.profile_workload == "torus_box_144_nb18":
+        p = W.torus_box(seed=3, nb=8, n_b=18, radius=0.3 * 144, sigma=0.06 * 144, order=8, n_levels=3)
     npts = p.n_points
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
