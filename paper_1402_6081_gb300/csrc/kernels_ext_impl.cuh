@@ -84,7 +84,7 @@ cudaError_t LaunchExt<T>::mac_persist(const void* fh, const void* kh, void* uh, 
             case 20: return launch_mac_persist_form<20>(fh, kh, uh, pp, early, st);
             case 24: return launch_mac_persist_form<24>(fh, kh, uh, pp, early, st);
             case 28: return launch_mac_persist_form<28>(fh, kh, uh, pp, early, st);
-            default: return cudaErrorInvalidValue;
+            default: return mac_persist_large(fh, kh, uh, pp, S, early, st);
         }
     }
 }

@@ -174,6 +174,10 @@ struct LaunchExt {
 };
 // Transform lengths the persistent products kernel is built for (FP32)
 bool persist_supported(int S);
+// the even lengths 38..66 of the block sizes 18..32 (kernels_persist_large.cu)
+bool persist_large_supported(int S);
+cudaError_t mac_persist_large(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S, int early,
+                              cudaStream_t st);
 
 // The steps of a solve with every size a run-time argument (generic.cu), for
 // the block sizes without per-size kernels (even n_b of [18, 32]).  The

@@ -73,7 +73,7 @@ def _mix(n_b):
 
 
 @pytest.mark.parametrize("prec", [lgfm.LGF_FP32, lgfm.LGF_FP64])
-@pytest.mark.parametrize("n_b", [8, 16])
+@pytest.mark.parametrize("n_b", [8, 16, 20])     # 20: the run-time-size kernels
 @pytest.mark.parametrize("separate", [0, 1])
 @pytest.mark.parametrize("same", [True, False])
 def test_multi_plan_matches_each_problem_alone(prec, n_b, separate, same):

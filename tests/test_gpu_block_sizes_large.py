@@ -99,6 +99,18 @@ def test_schedules_and_forms_nb18(opts):
         assert e <= tol, (prec, opts, mode, e)
 
 
+@pytest.mark.parametrize("n_b", [24, 32])
+@pytest.mark.parametrize("ik", [4, 5])
+def test_persistent_products_large_lengths(n_b, ik):
+    # the persistent products kernel at every level (interval_kernel 4: one
+    # FMA per real product, 5: packed), transform lengths 48 / 50 (n_b = 24)
+    # and 64 / 66 (n_b = 32); FP32 only
+    p, ref = subset_torus(n_b)
+    e = fmm.rel_linf(solve(p, lgfm.LGF_FP32, interval_kernel=ik), ref)
+    record_error(f"subset_torus_nb{n_b}_persist{ik}", fp32_vs_oracle=e)
+    assert e <= TOL32, e
+
+
 def test_manufactured_nb20():
     # exact answer known (Sec. 4.1).  The random source (the Laplacian of
     # noise) is badly conditioned, so the FP64 difference from the oracle is
