@@ -485,7 +485,7 @@ def error_sweep_run(torch, lgfm, diameter: int = 128):
     return out
 
 
-def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
+def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200, precisions=None, server_opts=None):
     """Poisson arrivals (200/s, seed 1) of torus solves with point counts
     log-uniform in 2^12..2^24, admitted under a 120 GB HBM budget, FP32 form
     and plain FP64 form, plus one 512^3 fully occupied solve in the stream and
@@ -501,9 +501,9 @@ def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
     reqs.append(Request(n_requests, t_big, big, problems[big].n_points))
     npts = {r.rid: r.n_points for r in reqs}
     out = {}
-    for prec in (lgfm.LGF_FP32, lgfm.LGF_FP64):
+    for prec in precisions or (lgfm.LGF_FP32, lgfm.LGF_FP64):
         name = "fp32" if prec == lgfm.LGF_FP32 else "fp64"
-        srv = GpuServer(prec, problems, budget_bytes=120e9, n_streams=16)
+        srv = GpuServer(prec, problems, budget_bytes=120e9, n_streams=16, **(server_opts or {}))
         srv.warm(shapes + [big])
         done, rejected = srv.run(reqs)
         timed = [d for d in done if n_warm <= d.rid < n_requests]
@@ -541,7 +541,9 @@ def serve_run(torch, lgfm, n_requests: int = 2200, n_warm: int = 200):
         out[name] = s
     out["config"] = {"workload": "serve_poisson200", "requests_timed": n_requests - n_warm, "warmup": n_warm,
                      "shapes": len(shapes), "hbm_budget_gb": 120, "streams": 16,
-                     "latency": "arrival to result in pinned host memory"}
+                     "latency": "arrival to result in pinned host memory",
+                     "large_requests": "more than 2^25 points: default-priority stream, plan leaves 32 SMs free "
+                                       "(others on high-priority streams)"}
     return out
 
 

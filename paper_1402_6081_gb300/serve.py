@@ -293,11 +293,20 @@ class GpuServer:
     k).  k is limited so that the folded plan picks the same product-kernel
     form at every level as the plan of one request (the persistent form is
     chosen per level by its number of sibling groups, 48 or more), so every
-    folded result has the bits of the same request solved alone."""
+    folded result has the bits of the same request solved alone.
+
+    Large requests (more than big_points points) run on a stream of the
+    default priority and their plans leave big_free_sms SMs to everything
+    else (option free_sms, unless the tuned options set it): the persistent
+    products of a large solve would otherwise hold every SM for milliseconds,
+    and the requests that arrive meanwhile (their streams at high priority)
+    would wait for them.  The large solve itself takes longer; the others see
+    the free SMs."""
 
     def __init__(self, precision: int, problems: dict, budget_bytes: float = 120e9, n_streams: int = 16,
                  tuned_options=None, source=None, keep_results: bool = False, background_plans: bool = True,
-                 fold_max: int = 8, fold_points: int = 1 << 18):
+                 fold_max: int = 8, fold_points: int = 1 << 18, big_points: int = 1 << 25,
+                 big_free_sms: int = 32):
         import concurrent.futures
 
         import torch
@@ -309,7 +318,10 @@ class GpuServer:
         self.dtype = torch.float64 if precision == lgfm.LGF_FP64 else torch.float32
         self.problems = problems
         self.tuned = tuned_options or {}
-        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.streams = [torch.cuda.Stream(priority=-1) for _ in range(n_streams)]   # high priority
+        self.big_stream = torch.cuda.Stream(priority=0)
+        self.big_points = big_points
+        self.big_free_sms = big_free_sms
         self.next_stream = 0
         self.source = source
         self.host_f = {} if source else {k: torch.from_numpy(p.f).to(self.dtype).pin_memory()
@@ -359,7 +371,9 @@ class GpuServer:
         self.torch.cuda.set_device(self.device)     # also on the plan-making thread
         shape, k = self._split(key)
         p = self.problems[shape]
-        opts = self.tuned.get(shape, {})
+        opts = dict(self.tuned.get(shape, {}))
+        if self.points(key) > self.big_points and "free_sms" not in opts:
+            opts["free_sms"] = self.big_free_sms
         if k == 1:
             s = self.lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, self.precision, **opts)
             st = s.stats()
@@ -383,8 +397,11 @@ class GpuServer:
 
     def submit(self, slot, reqs):
         s, f, u, uh = slot.handle
-        st = self.streams[self.next_stream]
-        self.next_stream = (self.next_stream + 1) % len(self.streams)
+        if self.points(slot.key) > self.big_points:
+            st = self.big_stream
+        else:
+            st = self.streams[self.next_stream]
+            self.next_stream = (self.next_stream + 1) % len(self.streams)
         nb = f.shape[0] // len(reqs)
         with self.torch.cuda.stream(st):
             for i, req in enumerate(reqs):
