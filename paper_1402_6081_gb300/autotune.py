@@ -52,6 +52,13 @@ def candidates(n_b: int, precision: int):
             v = [0, 1]
         if name == "fft_kernel" and n_b not in (8, 16):
             v = [0]
+        # block sizes of the run-time-size kernels: the reduced tables and the
+        # chunk size of the one-CTA-per-chunk products do not apply, and the
+        # product-kernel choice is persistent (0) or not (1)
+        if n_b > 16 and name in ("symmetric_spectra", "mac_groups_per_cta"):
+            v = [0]
+        if n_b > 16 and name == "interval_kernel":
+            v = [0, 1]
         if len(v) > 1:
             dims.append((name, v))
     return dims

@@ -35,11 +35,3 @@ def test_tuned_options_solve_the_same_problem(tmp_path, monkeypatch):
     ref = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order)
     assert fmm.rel_linf(u.double().cpu().numpy(), ref) <= 1e-5
     s.close()
-
-
-def test_search_space():
-    d16 = dict(autotune.candidates(16, lgfm.LGF_FP32))
-    assert d16["fft_size_interval"] == [0, 34, 36] and d16["fft_kernel"] == [0, 2]
-    assert d16["symmetric_spectra"] == [0, 1] and d16["mac_groups_per_cta"] == [0, 8, 32, 128]
-    d64 = dict(autotune.candidates(10, lgfm.LGF_FP64))
-    assert "fft_kernel" not in d64 and "free_sms" not in d64 and d64["interval_kernel"] == [0, 1]
