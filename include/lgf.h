@@ -112,9 +112,10 @@ typedef enum {
  *   n_blocks      >= 1
  *   n_b           points per block edge, even, 4 <= n_b <= 32 (odd or out of
  *                 range: LGF_ERR_INVALID_ARG).  4 .. 16 run kernels built per
- *                 size (transforms in shared memory); 18 .. 32 run kernels
- *                 with run-time sizes (transforms one axis per launch through
- *                 a device scratch, several times slower per point).  The
+ *                 size (transforms in shared memory; in FP32 also 18 and 20);
+ *                 the other steps of 18 .. 32 run kernels with run-time sizes
+ *                 (transforms one axis per launch through a device scratch),
+ *                 2-4 times slower per point.  The
  *                 tensor-core interpolation modes need 4, 8 or 16.
  *   n_levels      L >= 1: the leaves are level 1 and the root level is L
  *                 (Sec. 3.1).  Level L must hold intervals that are all near
@@ -141,8 +142,9 @@ lgf_status lgf_plan_create(const int32_t *block_ijk, int64_t n_blocks, int32_t n
  *   fft_size_interval  FFT length per axis S_I at levels >= 1 (Sec. 2.2: any
  *                      S_I >= 2 n_I - 1 gives the same linear convolution).
  *                      0 = default.  Supported: n_b = 4: 10; 6: 16; 8: 17,
- *                      18; 10: 24; 12: 28; 14: 32; 16: 33, 34, 36; 18 .. 32:
- *                      2 n_b + 2 (the default).  The level-0 length is 2 n_b.
+ *                      18; 10: 24; 12: 28; 14: 32; 16: 33, 34, 36; 18: 40;
+ *                      20 .. 32: 2 n_b + 2 (the default).  The level-0 length
+ *                      is 2 n_b.
  *   near_kernel        must be 0 (one product kernel for the level-0 near
  *                      field of the separate form: the 4^3 source blocks of a
  *                      sibling group, fully unrolled)

@@ -52,11 +52,11 @@ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
 // ---- twiddle tables ----
 // every transform length S of the supported block sizes (level 0: 2 n_b;
 // levels >= 1: the interval lengths)
-constexpr int kTwSizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36};
+constexpr int kTwSizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36, 40, 42};
 constexpr int kTwCount = int(sizeof(kTwSizes) / sizeof(kTwSizes[0]));
 // the i-th size of kTwSizes, usable in device code
 __host__ __device__ constexpr int tw_size(int i) {
-    constexpr int sizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36};
+    constexpr int sizes[] = {8, 10, 12, 16, 17, 18, 20, 24, 28, 32, 33, 34, 36, 40, 42};
     return sizes[i];
 }
 // offset of size S in the tables: the sizes above, laid end to end (-1 if absent)

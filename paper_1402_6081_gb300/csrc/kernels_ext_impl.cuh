@@ -44,6 +44,7 @@ cudaError_t LaunchExt<T>::r2c(int S, int n_in, const T* src, int64_t stride, con
     LGF_R2C(16, 7) LGF_R2C(24, 11) LGF_R2C(28, 13) LGF_R2C(32, 15)     // intervals
     LGF_R2C(16, 6) LGF_R2C(24, 10) LGF_R2C(28, 12) LGF_R2C(32, 14)     // level 1 from the blocks
 #undef LGF_R2C
+    if constexpr (sizeof(T) == 4) return r2c_large(S, n_in, src, stride, items, n, spec, st);
     return cudaErrorInvalidValue;
 }
 
@@ -55,6 +56,7 @@ cudaError_t LaunchExt<T>::c2r(int S, int n_out, const void* spec, const C2RItem*
     LGF_C2R(12, 6) LGF_C2R(20, 10) LGF_C2R(24, 12) LGF_C2R(28, 14)
     LGF_C2R(16, 7) LGF_C2R(24, 11) LGF_C2R(28, 13) LGF_C2R(32, 15)
 #undef LGF_C2R
+    if constexpr (sizeof(T) == 4) return c2r_large(S, n_out, spec, items, n, dst, ds, add, add_n, as, st);
     return cudaErrorInvalidValue;
 }
 

@@ -174,6 +174,14 @@ struct LaunchExt {
 };
 // Transform lengths the persistent products kernel is built for (FP32)
 bool persist_supported(int S);
+// Per-block transforms of the FP32 block sizes 18 and 20 (kernels_fft_large.cu):
+// (S, n) = (36, 18), (40, 18..20), (42, 20..21); own twiddle tables
+bool fft_large_supported(int S, int n);
+cudaError_t fft_large_init_twiddles();
+cudaError_t r2c_large(int S, int n_in, const float* src, int64_t stride, const R2CItem* items, int n, void* spec,
+                      cudaStream_t st);
+cudaError_t c2r_large(int S, int n_out, const void* spec, const C2RItem* items, int n, float* dst, int64_t ds,
+                      const float* add, int add_n, int64_t as, cudaStream_t st);
 // the even lengths 38..66 of the block sizes 18..32 (kernels_persist_large.cu)
 bool persist_large_supported(int S);
 cudaError_t mac_persist_large(const void* fh, const void* kh, void* uh, const PersistPlan& pp, int S, int early,

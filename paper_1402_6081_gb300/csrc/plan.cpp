@@ -55,7 +55,8 @@ int s_interval(int n_b) {
         case 12: return 28;
         case 14: return 32;
         case 16: return 33;
-        default: return 2 * n_b + 2;   // the run-time-size kernels (n_b 18..32)
+        case 18: return 40;            // 2 n_I + 2 would be 38 = 2 x 19: 40 has the FP32 per-block transform
+        default: return 2 * n_b + 2;   // the run-time-size kernels (n_b 20..32; 20 and FP32: per-block)
     }
 }
 static bool s_interval_supported(int n_b, int S) {
@@ -553,6 +554,7 @@ static lgf_status ensure_twiddles(int device, int prec) {
     cudaError_t e = prec == LGF_FP64 ? Launch<double>::init_twiddles() : Launch<float>::init_twiddles();
     if (e == cudaSuccess)
         e = prec == LGF_FP64 ? LaunchExt<double>::init_twiddles() : LaunchExt<float>::init_twiddles();
+    if (e == cudaSuccess && prec == LGF_FP32) e = fft_large_init_twiddles();
     if (e != cudaSuccess) return cuda_fail(e, "twiddle upload");
     g_tw_done.insert({device, prec});
     return ok();
@@ -1108,9 +1110,12 @@ static lgf_status build_plan(lgf_plan_s* P, const std::vector<HostPlan>& hp) {
             }
         }
         // transform scratch of each level: its larger item list, n_I planes
+        // (none where the FP32 per-block transforms serve the level)
         for (int l = 0; l <= Lmac; ++l) {
             DevLevel& D = P->lev[size_t(l)];
             const int S = l == 0 ? P->S0 : P->SI;
+            if (P->prec == LGF_FP32 && fft_large_supported(S, nb) && (l == 0 || fft_large_supported(S, nI)))
+                continue;
             const size_t items = size_t(std::max({D.n_r2c, D.n_c2r, l == 0 ? P->n_out : 0}));
             if ((s = dalloc(P, items * size_t(nI) * size_t(S) * size_t(S / 2 + 1) * 2 * elem, &D.gs, false)) !=
                 LGF_OK)
@@ -1171,13 +1176,17 @@ static lgf_status solve_impl(lgf_plan_s* P, const T* f, T* u, cudaStream_t st) {
     // pass the transforms through the level's other spectrum buffer.
     const bool gen = P->generic;
     using Gn = Generic<T>;
+    // (the FP32 sizes 18 and 20 keep the per-block transforms, whose cubes fit)
+    auto per_block = [&](int S, int n) { return sizeof(T) == 4 && fft_large_supported(S, n); };
     auto r2c_of = [&](int S, int n_in, const T* src, int64_t stride, DevLevel& D, cudaStream_t s) {
-        if (gen) return Gn::r2c(S, n_in, src, stride, D.r2c, D.n_r2c, D.fh, D.gs, P->tw_dev.at(S), s);
+        if (gen && !per_block(S, n_in))
+            return Gn::r2c(S, n_in, src, stride, D.r2c, D.n_r2c, D.fh, D.gs, P->tw_dev.at(S), s);
         return Lc::r2c(S, n_in, src, stride, D.r2c, D.n_r2c, D.fh, s);
     };
     auto c2r_of = [&](int S, int n_out, DevLevel& D, const C2RItem* items, int n, T* dst, int64_t ds, const T* add,
                       int add_n, int64_t as, cudaStream_t s) {
-        if (gen) return Gn::c2r(S, n_out, D.uh, items, n, D.gs, dst, ds, add, add_n, as, P->tw_dev.at(S), s);
+        if (gen && !per_block(S, n_out))
+            return Gn::c2r(S, n_out, D.uh, items, n, D.gs, dst, ds, add, add_n, as, P->tw_dev.at(S), s);
         return Lc::c2r(S, n_out, D.uh, items, n, dst, ds, add, add_n, as, s);
     };
     auto reg_of = [&](int l, int nm, const T* src, int from_blocks, const int* child, const int* parent, int n, T* dst,
