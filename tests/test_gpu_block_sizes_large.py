@@ -77,6 +77,24 @@ def test_subset_torus_against_oracle(n_b):
     assert e64 <= TOL64 and e32 <= TOL32, (e64, e32)
 
 
+@pytest.mark.parametrize("n_b", [18, 24])
+def test_four_levels_against_oracle(n_b):
+    # four levels: Reg from level-2 intervals into level 3 and Interp into the
+    # level-2 field (not only from and into blocks) on these kernels
+    box = W.torus_box(seed=77, nb=12, n_b=n_b, radius=0.3 * 12 * n_b, sigma=0.08 * 12 * n_b, order=8,
+                      n_levels=4)
+    p = W.block_subset(box, 0.2, seed=5)
+    ref = fmm.fmm_solve(p.blocks, p.f, p.n_b, p.n_levels, p.order)
+    s = lgfm.Solver(p.blocks, p.n_b, p.n_levels, p.order, lgfm.LGF_FP32)
+    st = s.stats()
+    s.close()
+    assert st["top_product_level"] >= 3
+    e64 = fmm.rel_linf(solve(p, lgfm.LGF_FP64), ref)
+    e32 = fmm.rel_linf(solve(p, lgfm.LGF_FP32), ref)
+    record_error(f"subset_torus_nb{n_b}_L4", fp64_vs_oracle=e64, fp32_vs_oracle=e32)
+    assert e64 <= TOL64 and e32 <= TOL32, (e64, e32)
+
+
 @pytest.mark.parametrize("opts", [{"separate_level1": 1}, {"interval_kernel": 1}, {"interval_kernel": 4},
                                   {"single_stream": 1, "free_sms": 24}, {"free_sms": -1},
                                   {"interp_mode": lgfm.LGF_INTERP_COMPENSATED}])
