@@ -416,6 +416,34 @@ lgf_status lgf_plan_timings(lgf_plan plan, int32_t max_kernels, int32_t *n_kerne
                             double *total_ms, int32_t *count, int32_t *launches_per_solve);
 
 /*
+ * lgf_conv_blocks - the FFT convolution of isolated blocks (the special case
+ * of Sec. 4.2, "FFT Conv.": the whole active grid is one block, and the method
+ * reduces to one zero-padded FFT convolution, Eqs. alg_upfft, alg_mult,
+ * alg_dwfft): u_b = G * f_b over block b alone, for every block b, in one
+ * kernel launch.  A CTA takes a block through the forward transform, the
+ * product with the block's own kernel spectrum and the inverse transform with
+ * the spectrum in shared memory (it never reaches device memory); the results
+ * equal those of a one-block plan and of lgf_solve_blocks_noalloc.
+ *
+ *   f_dev, u_dev  device pointers, n_blocks * n_b^3 values of the precision,
+ *                 block-major with x fastest (as lgf_solve); f_dev == u_dev
+ *                 (in place) is allowed, any other overlap of the two byte
+ *                 ranges is LGF_ERR_INVALID_ARG
+ *   n_blocks      1 .. 2^31 - 1
+ *   n_b           4, 8 or 16 (else LGF_ERR_UNSUPPORTED); precision
+ *                 LGF_FP32 or LGF_FP64
+ *   stream        cudaStream_t; the launch is asynchronous
+ *
+ * The first call on a device for an (n_b, precision) computes the kernel
+ * spectrum (FP64 on the host), allocates it on the device and uploads it with
+ * a synchronous copy (it stays until the process exits); make that first call
+ * before any stream capture.  Errors: LGF_ERR_OOM if that allocation fails,
+ * LGF_ERR_CUDA for a launch failure.
+ */
+lgf_status lgf_conv_blocks(const void *f_dev, void *u_dev, int64_t n_blocks, int32_t n_b, int32_t precision,
+                           void *stream);
+
+/*
  * lgf_solve_blocks_noalloc - solves every block as its own isolated problem,
  * u_b = G * f_b over block b alone (each block is a separate one-block domain,
  * as lgf_solve computes for a one-block plan), without allocating any device

@@ -61,6 +61,8 @@ _SIGS = {
     "lgf_plan_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "lgf_conv_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_void_p]),
     "lgf_solve_blocks_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "lgf_noalloc_max_blocks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
@@ -332,6 +334,12 @@ def lgf_measure_fma_peak(kind: int, reps: int = 5) -> tuple[float, float]:
     r, ms = ctypes.c_double(), ctypes.c_double()
     _check(library().lgf_measure_fma_peak(kind, reps, ctypes.byref(r), ctypes.byref(ms)), "lgf_measure_fma_peak")
     return r.value, ms.value
+
+
+def lgf_conv_blocks(f, u, n_blocks: int, n_b: int, precision: int, stream=None) -> None:
+    """FFT convolution of every block as its own one-block domain, in one kernel."""
+    _check(library().lgf_conv_blocks(_dev_ptr(f), _dev_ptr(u), n_blocks, n_b, precision, _stream_ptr(stream)),
+           "lgf_conv_blocks")
 
 
 def lgf_solve_blocks_noalloc(f, u, n_blocks: int, n_b: int, precision: int, stream=None) -> None:

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + ARCH
 SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_ext_f32.cu", "kernels_ext_f64.cu", "interp_tc.cu",
-           "noalloc.cu", "selftest.cu", "peak.cu", "generic.cu", "kernels_persist_large.cu", "kernels_fft_large.cu", "plan.cpp", "batch.cpp", "green.cpp", "host_fft.cpp",
+           "noalloc.cu", "selftest.cu", "peak.cu", "generic.cu", "kernels_persist_large.cu", "kernels_fft_large.cu", "fftconv.cu", "plan.cpp", "batch.cpp", "green.cpp", "host_fft.cpp",
            "select.cpp"]
 
 
