@@ -591,9 +591,11 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the n_max = 10 error sweep")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
-    ap.add_argument("--profile-workload", default=WORKLOAD, choices=[WORKLOAD, "torus_box_144_nb18"],
+    ap.add_argument("--profile-workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "torus_box_144_nb18", "fft_conv_16cubed_blocks"],
                     help="with --profile-only: the workload solved (torus_box_144_nb18: 8^3 blocks of 18^3, "
-                         "3 levels, the run-time-size kernels)")
+                         "3 levels, the run-time-size kernels; fft_conv_16cubed_blocks: the 512 blocks of the "
+                         "128^3 torus each alone, lgf_conv_blocks)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -624,6 +626,13 @@ def main():
     p = W.config(1)
     if args.profile_only and args.profile_workload == "torus_box_144_nb18":
         p = W.torus_box(seed=3, nb=8, n_b=18, radius=0.3 * 144, sigma=0.06 * 144, order=8, n_levels=3)
+    if args.profile_only and args.profile_workload == "fft_conv_16cubed_blocks":
+        fc = torch.from_numpy(p.f).float().cuda()
+        uc = torch.empty_like(fc)
+        for _ in range(args.warmup + args.steps):
+            lgfm.lgf_conv_blocks(fc, uc, len(p.blocks), p.n_b, lgfm.LGF_FP32)
+        torch.cuda.synchronize()
+        return
     npts = p.n_points
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
