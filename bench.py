@@ -592,10 +592,11 @@ def main():
     ap.add_argument("--profile-only", action="store_true",
                     help="only warmup + steps of the FP32 solve (for ncu captures); prints no JSON")
     ap.add_argument("--profile-workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "torus_box_144_nb18", "fft_conv_16cubed_blocks"],
+                    choices=[WORKLOAD, "torus_box_144_nb18", "fft_conv_16cubed_blocks", "tori_irregular_512"],
                     help="with --profile-only: the workload solved (torus_box_144_nb18: 8^3 blocks of 18^3, "
                          "3 levels, the run-time-size kernels; fft_conv_16cubed_blocks: the 512 blocks of the "
-                         "128^3 torus each alone, lgf_conv_blocks)")
+                         "128^3 torus each alone, lgf_conv_blocks; tori_irregular_512: the 5-level irregular "
+                         "domain)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -626,6 +627,8 @@ def main():
     p = W.config(1)
     if args.profile_only and args.profile_workload == "torus_box_144_nb18":
         p = W.torus_box(seed=3, nb=8, n_b=18, radius=0.3 * 144, sigma=0.06 * 144, order=8, n_levels=3)
+    if args.profile_only and args.profile_workload == "tori_irregular_512":
+        p = W.config(2)
     if args.profile_only and args.profile_workload == "fft_conv_16cubed_blocks":
         fc = torch.from_numpy(p.f).float().cuda()
         uc = torch.empty_like(fc)
